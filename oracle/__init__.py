@@ -1,0 +1,332 @@
+"""CPU oracle for the BayesFusion-SDF posterior solve -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+arm may import this package.  The product path (the CUDA library and its
+Python binding) never imports, links or runs it, and the two share no code.
+
+The arithmetic lives in ``bfo.c`` (plain C, FP64 for every real-valued
+quantity, a fixed FP32 specification for discrete decisions; every function
+there cites the section of the paper it restates).  This module compiles it
+with gcc and marshals numpy arrays through ctypes; it computes nothing.
+
+Parity status: every function is pinned by the ``-m "not gpu"`` tests against
+closed forms, invariants, special cases or brute force (see
+tests/test_oracle_*.py); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bfo.c")
+_LIB = os.path.join(_HERE, "_bfo.so")
+_lib = None
+
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+c_dp = ctypes.POINTER(ctypes.c_double)
+c_fp = ctypes.POINTER(ctypes.c_float)
+
+
+class _Band(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nb", ctypes.c_int), ("h", ctypes.c_float),
+                ("org", ctypes.c_float * 3), ("N", ctypes.c_int64), ("NB", ctypes.c_int32),
+                ("n_cand", ctypes.c_int64),
+                ("dir", ctypes.POINTER(ctypes.c_int32)), ("bcoord", ctypes.POINTER(ctypes.c_int32)),
+                ("mask", ctypes.POINTER(ctypes.c_uint64)), ("off", c_i64p), ("lin", c_i64p),
+                ("tsdf", c_fp), ("wcount", ctypes.POINTER(ctypes.c_int32)),
+                ("bdry", ctypes.POINTER(ctypes.c_uint8)), ("deg", ctypes.POINTER(ctypes.c_uint8)),
+                ("nbr", ctypes.POINTER(ctypes.c_int32))]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle in-tree (gcc, FP contraction off, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-fopenmp", "-std=c11", "-D_DEFAULT_SOURCE", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    L = ctypes.CDLL(_LIB)
+    bp = ctypes.POINTER(_Band)
+    f, i, d, u64, i64 = ctypes.c_float, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64
+    L.bfo_build_band.restype = bp
+    L.bfo_build_band.argtypes = [c_fp, i, i, i, c_fp, f, f, f, f, i, f, c_fp, d, d, i]
+    L.bfo_band_free.argtypes = [bp]
+    L.bfo_band_index.restype = i64
+    L.bfo_band_index.argtypes = [bp, i, i, i]
+    L.bfo_integrate.argtypes = [bp, c_fp, i, i, i, c_fp, f, f, f, f, d, d, d, d, d, c_dp, c_dp, c_i64p]
+    L.bfo_dda_trace.restype = i64
+    L.bfo_dda_trace.argtypes = [bp, c_fp, f, f, f, f, i, i, f, d, c_i64p, i64]
+    L.bfo_assemble.argtypes = [bp, c_dp, c_dp, d, d, c_dp, c_dp]
+    L.bfo_spmv.argtypes = [bp, d, c_dp, c_dp, c_dp]
+    L.bfo_csr.restype = i64
+    L.bfo_csr.argtypes = [bp, d, c_dp, c_i64p, c_i64p, c_dp]
+    L.bfo_pcg.restype = i
+    L.bfo_pcg.argtypes = [bp, d, c_dp, c_dp, c_dp, d, i, c_dp, ctypes.POINTER(i), c_dp]
+    L.bfo_splitmix64.restype = u64
+    L.bfo_splitmix64.argtypes = [u64]
+    L.bfo_probe.argtypes = [u64, u64, i64, c_i64p, c_dp]
+    L.bfo_hutchinson.restype = i
+    L.bfo_hutchinson.argtypes = [bp, d, c_dp, i, u64, d, i, i, c_dp, ctypes.POINTER(i), c_dp, i]
+    L.bfo_mc_case.restype = i
+    L.bfo_mc_case.argtypes = [i, ctypes.POINTER(ctypes.c_int32)]
+    L.bfo_mc.argtypes = [bp, c_fp, c_i64p, ctypes.POINTER(c_dp), c_i64p,
+                         ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
+    L.bfo_free.argtypes = [ctypes.c_void_p]
+    L.bfo_predict_depth.argtypes = [bp, c_fp, c_fp, f, f, f, f, i, i, c_fp]
+    L.bfo_score_views.restype = i
+    L.bfo_score_views.argtypes = [bp, c_fp, c_dp, c_dp, c_fp, i, f, f, f, f, i, i, d, d, d, d, d, d, c_dp]
+    _lib = L
+    return L
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, np.float64)
+
+
+@dataclass
+class Band:
+    """Oracle band: brick directory and compact band arrays (numpy copies)."""
+    n: int
+    h: float
+    origin: tuple
+    N: int
+    NB: int
+    n_cand: int
+    dir: np.ndarray       # int32 [nb^3]
+    bcoord: np.ndarray    # int32 [NB,3]
+    mask: np.ndarray      # uint64 [NB,8]
+    off: np.ndarray       # int64 [NB+1]
+    lin: np.ndarray       # int64 [N]
+    tsdf: np.ndarray      # float32 [N] metres
+    wcount: np.ndarray    # int32 [N]
+    bdry: np.ndarray      # uint8 [N]
+    deg: np.ndarray       # uint8 [N]
+    nbr: np.ndarray       # int32 [NB,6]
+    _ptr: object = None
+
+    def __del__(self):
+        if self._ptr is not None and _lib is not None:
+            _lib.bfo_band_free(self._ptr)
+            self._ptr = None
+
+    def index(self, i, j, k) -> int:
+        return int(_lib.bfo_band_index(self._ptr, i, j, k))
+
+    def ijk(self) -> np.ndarray:
+        n = self.n
+        L = self.lin
+        return np.stack([L % n, (L // n) % n, L // (n * n)], 1)
+
+    def centres(self) -> np.ndarray:
+        return np.asarray(self.origin, np.float64) + (self.ijk() + 0.5) * self.h
+
+
+def build_band(depth, poses, intr, n, h, origin, band_vox, trunc_vox, threads=0) -> Band:
+    L = _load()
+    depth, poses = _f32(depth), _f32(poses)
+    fx, fy, cx, cy, W, H = intr
+    T = depth.shape[0]
+    org = _f32(origin)
+    ptr = L.bfo_build_band(_p(depth, ctypes.c_float), T, H, W, _p(poses, ctypes.c_float), fx, fy, cx, cy,
+                           n, h, _p(org, ctypes.c_float), band_vox, trunc_vox, threads)
+    b = ptr.contents
+    N, NB, nb = b.N, b.NB, b.nb
+
+    def cp(p, cnt, dt):
+        return np.ctypeslib.as_array(p, shape=(max(cnt, 1),))[:cnt].astype(dt, copy=True)
+
+    return Band(n=n, h=float(np.float32(h)), origin=tuple(float(v) for v in org), N=N, NB=NB,
+                n_cand=b.n_cand, dir=cp(b.dir, nb ** 3, np.int32), bcoord=cp(b.bcoord, 3 * NB, np.int32).reshape(NB, 3),
+                mask=cp(b.mask, 8 * NB, np.uint64).reshape(NB, 8), off=cp(b.off, NB + 1, np.int64),
+                lin=cp(b.lin, N, np.int64), tsdf=cp(b.tsdf, N, np.float32), wcount=cp(b.wcount, N, np.int32),
+                bdry=cp(b.bdry, N, np.uint8), deg=cp(b.deg, N, np.uint8), nbr=cp(b.nbr, 6 * NB, np.int32).reshape(NB, 6),
+                _ptr=ptr)
+
+
+def build_band_w(w, threads=0) -> Band:
+    return build_band(w.depth, w.poses, w.intr, w.n, w.h, w.origin, w.band_vox, w.trunc_vox, threads)
+
+
+def integrate(band: Band, depth, poses, intr, band_vox, sig_a, sig_b, sig_pose=0.0, sig_model=0.0):
+    """Returns (d, hdata, stats) in voxel units, FP64."""
+    L = _load()
+    depth, poses = _f32(depth), _f32(poses)
+    fx, fy, cx, cy, W, H = intr
+    d = np.zeros(band.N, np.float64)
+    hd = np.zeros(band.N, np.float64)
+    st = np.zeros(2, np.int64)
+    L.bfo_integrate(band._ptr, _p(depth, ctypes.c_float), depth.shape[0], H, W, _p(poses, ctypes.c_float),
+                    fx, fy, cx, cy, band_vox, sig_a, sig_b, sig_pose, sig_model, _p(d, ctypes.c_double),
+                    _p(hd, ctypes.c_double), _p(st, ctypes.c_int64))
+    return d, hd, st
+
+
+def integrate_w(band, w):
+    return integrate(band, w.depth, w.poses, w.intr, w.band_vox, w.sig_a, w.sig_b, w.sig_pose, w.sig_model)
+
+
+def dda_trace(band: Band, pose, intr, px, py, D, band_vox, cap=4096) -> np.ndarray:
+    L = _load()
+    pose = _f32(pose)
+    fx, fy, cx, cy, W, H = intr
+    out = np.empty(cap, np.int64)
+    m = L.bfo_dda_trace(band._ptr, _p(pose, ctypes.c_float), fx, fy, cx, cy, px, py, D, band_vox,
+                        _p(out, ctypes.c_int64), cap)
+    return out[:m].copy()
+
+
+def assemble(band: Band, d, hd, lam, lam_b):
+    L = _load()
+    d, hd = _f64(d), _f64(hd)
+    qd = np.empty(band.N, np.float64)
+    rhs = np.empty(band.N, np.float64)
+    L.bfo_assemble(band._ptr, _p(d, ctypes.c_double), _p(hd, ctypes.c_double), lam, lam_b,
+                   _p(qd, ctypes.c_double), _p(rhs, ctypes.c_double))
+    return qd, rhs
+
+
+def spmv(band: Band, lam, qdiag, x) -> np.ndarray:
+    L = _load()
+    qdiag, x = _f64(qdiag), _f64(x)
+    y = np.empty(band.N, np.float64)
+    L.bfo_spmv(band._ptr, lam, _p(qdiag, ctypes.c_double), _p(x, ctypes.c_double), _p(y, ctypes.c_double))
+    return y
+
+
+def csr(band: Band, lam, qdiag):
+    """Q as (indptr, indices, data) numpy arrays."""
+    L = _load()
+    qdiag = _f64(qdiag)
+    nnz = L.bfo_csr(band._ptr, lam, _p(qdiag, ctypes.c_double), None, None, None)
+    rp = np.empty(band.N + 1, np.int64)
+    ci = np.empty(nnz, np.int64)
+    val = np.empty(nnz, np.float64)
+    L.bfo_csr(band._ptr, lam, _p(qdiag, ctypes.c_double), _p(rp, ctypes.c_int64), _p(ci, ctypes.c_int64),
+              _p(val, ctypes.c_double))
+    return rp, ci, val
+
+
+def dense_Q(band: Band, lam, qdiag) -> np.ndarray:
+    rp, ci, val = csr(band, lam, qdiag)
+    Q = np.zeros((band.N, band.N))
+    for r in range(band.N):
+        Q[r, ci[rp[r]:rp[r + 1]]] += val[rp[r]:rp[r + 1]]
+    return Q
+
+
+def pcg(band: Band, lam, qdiag, rhs, tol=1e-12, max_iter=20000, x0=None):
+    """Returns (x, status, iters, relres)."""
+    L = _load()
+    qdiag, rhs = _f64(qdiag), _f64(rhs)
+    x = np.empty(band.N, np.float64)
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    x0p = _p(_f64(x0), ctypes.c_double) if x0 is not None else None
+    if x0 is not None:
+        x0 = _f64(x0)
+        x0p = _p(x0, ctypes.c_double)
+    st = L.bfo_pcg(band._ptr, lam, _p(qdiag, ctypes.c_double), _p(rhs, ctypes.c_double), x0p, tol, max_iter,
+                   _p(x, ctypes.c_double), ctypes.byref(it), ctypes.byref(rr))
+    return x, st, it.value, rr.value
+
+
+def splitmix64(x: int) -> int:
+    return int(_load().bfo_splitmix64(x))
+
+
+def probe(seed: int, k: int, lin) -> np.ndarray:
+    lin = np.ascontiguousarray(lin, np.int64)
+    z = np.empty(len(lin), np.float64)
+    _load().bfo_probe(seed, k, len(lin), _p(lin, ctypes.c_int64), _p(z, ctypes.c_double))
+    return z
+
+
+def hutchinson(band: Band, lam, qdiag, K, seed, tol=1e-12, max_iter=20000, k0=0, keep=0):
+    """Returns (s, status, total_iters, per_probe_solutions[keep,N])."""
+    L = _load()
+    qdiag = _f64(qdiag)
+    s = np.empty(band.N, np.float64)
+    it = ctypes.c_int()
+    pp = np.empty((max(keep, 1), band.N), np.float64)
+    st = L.bfo_hutchinson(band._ptr, lam, _p(qdiag, ctypes.c_double), K, seed, tol, max_iter, k0,
+                          _p(s, ctypes.c_double), ctypes.byref(it), _p(pp, ctypes.c_double), keep)
+    return s, st, it.value, pp[:keep]
+
+
+def mc_case(cs: int) -> np.ndarray:
+    tri = np.zeros((16, 3), np.int32)
+    m = _load().bfo_mc_case(cs, _p(tri, ctypes.c_int32))
+    return tri[:m].copy()
+
+
+def marching_cubes(band: Band, mu):
+    """Returns (verts f64 [V,3] metres, tris int32 [F,3])."""
+    L = _load()
+    mu = _f32(mu)
+    nv, nt = ctypes.c_int64(), ctypes.c_int64()
+    vp, tp = c_dp(), ctypes.POINTER(ctypes.c_int32)()
+    L.bfo_mc(band._ptr, _p(mu, ctypes.c_float), ctypes.byref(nv), ctypes.byref(vp), ctypes.byref(nt),
+             ctypes.byref(tp))
+    V = np.ctypeslib.as_array(vp, shape=(max(nv.value, 1) * 3,))[:3 * nv.value].reshape(-1, 3).copy()
+    F = np.ctypeslib.as_array(tp, shape=(max(nt.value, 1) * 3,))[:3 * nt.value].reshape(-1, 3).copy()
+    L.bfo_free(ctypes.cast(vp, ctypes.c_void_p))
+    L.bfo_free(ctypes.cast(tp, ctypes.c_void_p))
+    return V, F
+
+
+def predict_depth(band: Band, mu, pose, intr) -> np.ndarray:
+    L = _load()
+    mu, pose = _f32(mu), _f32(pose)
+    fx, fy, cx, cy, W, H = intr
+    out = np.empty((H, W), np.float32)
+    L.bfo_predict_depth(band._ptr, _p(mu, ctypes.c_float), _p(pose, ctypes.c_float), fx, fy, cx, cy, W, H,
+                        _p(out, ctypes.c_float))
+    return out
+
+
+def score_views(band: Band, mu, s, qdiag, cand_poses, cand_intr, band_vox, sig_a, sig_b, sig_pose=0.0,
+                sig_model=0.0, eps=1.0):
+    """Returns (U f64 [V], best)."""
+    L = _load()
+    mu, s, qdiag, cand = _f32(mu), _f64(s), _f64(qdiag), _f32(cand_poses)
+    fx, fy, cx, cy, W, H = cand_intr
+    V = cand.shape[0]
+    U = np.zeros(V, np.float64)
+    best = L.bfo_score_views(band._ptr, _p(mu, ctypes.c_float), _p(s, ctypes.c_double), _p(qdiag, ctypes.c_double),
+                             _p(cand, ctypes.c_float), V, fx, fy, cx, cy, W, H, band_vox, sig_a, sig_b, sig_pose,
+                             sig_model, eps, _p(U, ctypes.c_double))
+    return U, best
+
+
+def solve_all(w, threads=0, tol=1e-12, K=None):
+    """Full oracle pipeline for a workload: band, d/h, Q, mu and (optionally) s."""
+    b = build_band_w(w, threads)
+    d, hd, st = integrate_w(b, w)
+    qd, rhs = assemble(b, d, hd, w.lam, w.lam_b)
+    mu, status, iters, rr = pcg(b, w.lam, qd, rhs, tol=tol)
+    out = dict(band=b, d=d, hd=hd, qdiag=qd, rhs=rhs, mu=mu, iters=iters, relres=rr, status=status)
+    if K:
+        s, st2, tot, _ = hutchinson(b, w.lam, qd, K, w.seed, tol=tol)
+        out.update(s=s, hutch_iters=tot)
+    return out

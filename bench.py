@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the narrow-band GRF posterior solve on one node.
+
+One step = the whole hot path on one synthetic depth sequence, inputs already
+resident in device memory: build_band -> integrate_depth -> solve_mean ->
+estimate_variance -> extract_surface -> score_views.  The headline metric
+is the posterior solve time (solve_mean + estimate_variance, FP32 vectors
+with FP64 dots and refinement, rel_tol 1e-6, 64 probes), read from CUDA
+events on the library's stream.  Also reported: the full step time, the
+same metric end to end through the C ABI with pinned host buffers (H2D of
+the frames and D2H of mu and s inside the timed region), the roofline of
+the dominant kernel (event-timed by bf_bench_kernel), and the CPU oracle
+timed on a bounded sample of the same workload.
+
+Multi-GPU: one process per GPU (torchrun); every rank solves its own
+instance of the workload (noise seed = rank) with no collective on the data
+path (replicas: the box has one GPU per solve); value = max-over-ranks time /
+posteriors solved.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "posterior solve s (mean+diag var) at 1e-6 rel residual; SpMV GB/s vs HBM peak"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="union256")
+    ap.add_argument("--K", type=int, default=64)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--rhs-block", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget (s)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [n for k, n in enumerate(names) if any(r[3 + k].lower() == "active" for r in rows)]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, v: float) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- oracle
+
+def oracle_sample(w, tol, K, budget_s):
+    """Time the oracle's posterior solve on a bounded sample: the mean solve
+    plus as many of the K probe solves as fit in budget_s; extrapolated
+    linearly to K probes."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    b = oracle.build_band_w(w)
+    d, hd, _ = oracle.integrate_w(b, w)
+    qd, rhs = oracle.assemble(b, d, hd, w.lam, w.lam_b)
+    t0 = time.perf_counter()
+    oracle.pcg(b, w.lam, qd, rhs, tol=tol)
+    t_mean = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    k = 0
+    while k < K and (k < 1 or time.perf_counter() - t1 < budget_s):
+        oracle.hutchinson(b, w.lam, qd, 1, w.seed, tol=tol, k0=k)
+        k += 1
+    t_probe = (time.perf_counter() - t1) / k
+    est = t_mean + K * t_probe
+    sample = (f"{w.name}: oracle mean solve + {k} of {K} probe solves at rel_tol {tol:g} on N={b.N} band "
+              f"voxels, FP64 CSR PCG; time extrapolated linearly to {K} probes")
+    return est, cores, sample, k
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import synth
+    w = synth.make_workload(args.workload)
+    vals = []
+    k_used = 0
+    cores, sample = 1, ""
+    for i in range(args.warmup + args.steps):
+        budget = max(2.0, args.cpu_seconds / max(args.steps, 1))
+        est, cores, sample, k_used = oracle_sample(w, args.tol, args.K, budget)
+        if i >= args.warmup:
+            vals.append(est)
+    v = statistics.mean(vals)
+    line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "K": args.K, "rel_tol": args.tol},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2602_19697_gb300 import bfsdf, build
+
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.make_workload(args.workload, seed=rank)
+    stream = torch.cuda.Stream(dev)
+    ctx = bfsdf.Context(local, stream.cuda_stream)
+    depth = torch.from_numpy(w.depth).to(dev)
+    poses = torch.from_numpy(w.poses).to(dev)
+    cand = torch.from_numpy(w.cand_poses).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    R = args.rhs_block
+
+    def step():
+        with torch.cuda.stream(stream):
+            return _step()
+
+    def _step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(stream)
+        band = ctx.build_band_w(w, depth, poses)
+        ev[1].record(stream)
+        band.integrate_depth(depth, poses, w.intr)
+        ev[2].record(stream)
+        mu = torch.empty(band.N, device=dev)
+        s = torch.empty(band.N, device=dev)
+        im = band.solve_mean(mu, rel_tol=args.tol)
+        iv = band.estimate_variance(s, K=args.K, seed=0, rel_tol=args.tol, rhs_block=R)
+        ev[3].record(stream)
+        V, F = band.extract_surface(mu, device=dev)
+        ev[4].record(stream)
+        U, best = band.score_views(mu, s, cand, w.cand_intr)
+        ev[5].record(stream)
+        stream.synchronize()
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+        info = dict(N=band.N, NB=band.NB, mean_iters=im.iters, var_iters=iv.iters, tris=int(F.shape[0]),
+                    best_view=best)
+        return band, t, info
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+
+    for _ in range(args.warmup):
+        b, _, _ = step()
+        b.free()
+        flush_l2()
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = bfsdf.launch_count()
+    times, info = [], None
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        b, t, info = step()
+        times.append(t)
+        b.free()
+        flush_l2()
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    launches = (bfsdf.launch_count() - l0) // max(args.steps, 1)
+    clocks = clk.stop()
+
+    post = [t[2] for t in times]            # solve_mean + estimate_variance (ms)
+    stepms = [sum(t) for t in times]
+    post_s = max_over_ranks(world, statistics.mean(post) / 1e3)
+    step_s = max_over_ranks(world, statistics.mean(stepms) / 1e3)
+    value = post_s / world                   # seconds per posterior across the job
+
+    # ---- roofline of the dominant kernel (block PCG SpMV), event-timed
+    hbm, peak_kind = peaks()
+    band = ctx.build_band_w(w, depth, poses)
+    band.integrate_depth(depth, poses, w.intr)
+    s = torch.empty(band.N, device=dev)
+    band.estimate_variance(s, K=R, seed=0, rel_tol=args.tol, rhs_block=R)
+    ms_blk = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_SPMV, R=R, reps=50)
+    N, NB = band.N, band.NB
+    # algorithmic bytes: per (voxel, column) r, p_in read + p_out, q written (16 B);
+    # per voxel qd (4 B); per brick 16 lookup words (128 B) + 6 neighbour ranks (24 B)
+    bytes_blk = N * R * 16 + N * 4 + NB * (128 + 24)
+    ms_spmv = band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=200)
+    bytes_spmv = N * 12 + NB * (128 + 24)   # x, qd read, y written; brick metadata
+    achieved = bytes_blk / (ms_blk * 1e-3) / 1e9
+    roof = {"kernel": "k_blk_spmv<%d> (block-PCG p-update + 7-point SpMM + p.q)" % R, "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+            "peak_kind": peak_kind, "traffic": None, "bytes_per_launch": bytes_blk,
+            "ms_per_launch": round(ms_blk, 5)}
+    spmv = {"kernel": "k_brick (7-point SpMV, single RHS)", "achieved": round(bytes_spmv / (ms_spmv * 1e-3) / 1e9, 1),
+            "ms_per_launch": round(ms_spmv, 5), "bytes_per_launch": bytes_spmv,
+            "note": "single-RHS vectors of this workload are L2-resident (%.1f MB)" % (N * 12 / 1e6)}
+    band.free()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        dh = torch.from_numpy(w.depth).pin_memory()
+        ph = torch.from_numpy(w.poses).pin_memory()
+        e2e_t = []
+        for i in range(2 + args.steps):
+            stream.synchronize()
+            t0 = time.perf_counter()
+            b = ctx.build_band_w(w, dh, ph)
+            b.integrate_depth(dh, ph, w.intr)
+            muh = torch.empty(b.N, dtype=torch.float32).pin_memory()
+            sh = torch.empty(b.N, dtype=torch.float32).pin_memory()
+            b.solve_mean(muh, rel_tol=args.tol)
+            b.estimate_variance(sh, K=args.K, seed=0, rel_tol=args.tol, rhs_block=R)
+            stream.synchronize()
+            dt = time.perf_counter() - t0
+            if i >= 2:
+                e2e_t.append(dt)
+            nb = b.N
+            b.free()
+        e2e_s = max_over_ranks(world, statistics.mean(e2e_t)) / world
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(2 * w.depth.nbytes + 2 * w.poses.nbytes),
+               "d2h_bytes_per_step": int(2 * nb * 4),
+               "note": "build_band + integrate_depth + solve_mean + estimate_variance from pinned host frames "
+                       "to host mu and s (frames staged by each of the two calls that read them)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        est, cores, sample, k = oracle_sample(w, args.tol, args.K, args.cpu_seconds)
+        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        mean_t = [statistics.mean(x) for x in zip(*times)]
+        line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{w.name}: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, "
+                                       f"{w.T} views {w.intr[4]}x{w.intr[5]}, K={args.K} probes, rel_tol {args.tol:g}",
+                           "N_band": info["N"], "bricks": info["NB"], "rhs_block": R,
+                           "l2": "512 MB buffer written between timed steps",
+                           "parallelism": f"replicas x{world}"},
+                "breakdown_ms": {"build_band": mean_t[0], "integrate_depth": mean_t[1],
+                                 "posterior_solve": mean_t[2], "extract_surface": mean_t[3],
+                                 "score_views": mean_t[4]},
+                "iters": {"mean": info["mean_iters"], "variance_total": info["var_iters"]},
+                "roofline": roof, "spmv": spmv, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "wall_s": round(wall, 3)}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * bfsdf.h -- C ABI of the GB300 narrow-band posterior solver for
+ * probabilistic signed-distance fusion (BayesFusion-SDF, arXiv 2602.19697).
+ *
+ * The library runs the method of Sec. 3 / Algorithm 1 of the paper on one
+ * GPU: coarse TSDF and narrow band (Sec. 3.3, steps 1-2), sparse 8^3 bricks
+ * (Sec. 3.4), depth-to-SDF observations (Sec. 3.5, step 3), the GMRF
+ * posterior Q = Q0 + A^T W A, h = A^T W y + b0 (Sec. 3.6, step 4), the MAP
+ * mean by PCG (Sec. 3.6, step 5), the probe estimate of diag(Q^-1) (Sec. 3.7,
+ * step 6), marching cubes (Sec. 3.8, step 7) and next-best-view utilities
+ * (Sec. 3.8, step 8).
+ *
+ * Conventions (all calls):
+ *  - Grid: cubic n^3 lattice (n a multiple of 8) of voxel size `voxel`
+ *    metres; voxel (i,j,k) has centre origin + (i + 1/2, j + 1/2, k + 1/2) h
+ *    and linear index i + n (j + n k).  Bricks are 8^3 voxels; brick (bi,bj,bk)
+ *    has linear index bi + nb (bj + nb bk), nb = n / 8.
+ *  - Band layout: the N band voxels are stored compactly, ordered by (brick
+ *    rank, local index lx + 8 ly + 64 lz), brick ranks ascending in linear
+ *    brick index.  Every per-voxel array of the API ([N]) uses this order.
+ *  - Units: the solver works in voxel units (paper's x divided by h): mu is
+ *    in voxels, s in voxels^2.  Multiply by h (h^2) for metres (m^2).
+ *    Camera poses are world<-camera [R | C] (row-major 3x4 floats), depth is
+ *    z-depth in metres, 0 or non-finite = invalid pixel, SDF > 0 on the
+ *    camera side.
+ *  - Memory: every array argument may be HOST or DEVICE memory (the library
+ *    asks the CUDA driver which).  Host inputs are staged through the
+ *    library's device workspace; host outputs are written back before the
+ *    call returns.  With device pointers only, calls are asynchronous on the
+ *    context's stream except where a size must come back to the host
+ *    (bf_build_band, bf_extract_surface, bf_score_views and the iteration
+ *    counts of the solvers).  The caller owns every array it passes; the
+ *    library owns the context, the band and their workspaces.
+ *  - Errors: every call returns a bf_status; BF_OK is 0.  The text of the
+ *    last error of a context is available from bf_last_error.  A call that
+ *    fails leaves its outputs unspecified but the context usable, except
+ *    after BF_ECUDA, which reports a CUDA error (the CUDA context may be lost).
+ */
+#ifndef BFSDF_H
+#define BFSDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_ctx bf_ctx;   /* one GPU + one CUDA stream + workspace */
+typedef struct bf_band bf_band; /* band, brick directory, system, solver state */
+
+typedef enum {
+  BF_OK = 0,
+  BF_EINVAL = 1,          /* bad argument (null pointer, size, range)        */
+  BF_ENOMEM = 2,          /* device allocation failed                        */
+  BF_ECUDA = 3,           /* CUDA runtime error                              */
+  BF_NOT_CONVERGED = 4,   /* iteration limit hit; best iterate written       */
+  BF_BREAKDOWN = 5,       /* PCG breakdown (p.Qp <= 0 or non-finite)         */
+  BF_ESTATE = 6           /* call order violated (e.g. solve before integrate) */
+} bf_status;
+
+typedef struct {
+  int n;            /* voxels per axis, multiple of 8, 8..2048             */
+  float voxel;      /* voxel size h in metres                              */
+  float origin[3];  /* world position of the grid corner (metres)          */
+} bf_grid;
+
+typedef struct {
+  float fx, fy, cx, cy; /* pinhole intrinsics (pixels)                       */
+  int W, H;             /* image size (pixels)                               */
+} bf_intrinsics;
+
+typedef struct {
+  double band_vox;   /* band half-width b (voxels): B = {|tsdf| <= b h}     */
+  double trunc_vox;  /* coarse TSDF truncation tau_c (voxels), > band_vox  */
+  double lambda;     /* smoothness weight (Sec. 3.6, Q0 equation)          */
+  double lambda_b;   /* boundary anchor weight (Sec. 3.6, Q0 equation)     */
+  double sig_a, sig_b;        /* sigma_depth(D) = sig_a + sig_b D^2 (m)    */
+  double sig_pose, sig_model; /* sigma_pose, sigma_model (m), Sec. 3.5     */
+} bf_params;
+
+/* bf_solve_mean / bf_estimate_variance flags */
+#define BF_SOLVE_FP64 1u  /* FP64 vectors and SpMV (default: FP32 vectors, FP64 inner products) */
+#define BF_SOLVE_WARM 2u  /* mu holds the initial guess on entry (default: x0 = 0)              */
+
+/* Create a context on CUDA device `device`, issuing work on `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  Returns BF_EINVAL for a
+ * null `out`, BF_ECUDA if the device cannot be used. */
+bf_status bf_create(int device, void* stream, bf_ctx** out);
+void bf_destroy(bf_ctx* ctx);
+const char* bf_last_error(const bf_ctx* ctx);
+bf_status bf_set_stream(bf_ctx* ctx, void* stream);
+
+/* Coarse TSDF bootstrap and narrow-band activation (Sec. 3.3, band equation
+ * with alpha = 1, tau = band_vox h) on a sparse lattice of 8^3 bricks
+ * (Sec. 3.4); Algorithm 1 steps 1-2.
+ *   depth [T][H][W] float z-depth (m); poses [T][3][4] world<-camera.
+ * TSDF: unit weight per frame, sample min(D - z_c, tau_c), samples below
+ * -tau_c skipped.  Only bricks within r_B = floor((1.25 trunc_vox + 2)/8) + 1
+ * bricks of a back-projected valid pixel are evaluated.  All decisions use
+ * IEEE FP32 with separately rounded operations, so the band is reproducible
+ * bit for bit.  *out receives a new band (free with bf_band_free).  Errors:
+ * BF_EINVAL (T < 1, n not a multiple of 8, band_vox <= 0, trunc_vox <=
+ * band_vox, null pointer), BF_ENOMEM. */
+bf_status bf_build_band(bf_ctx* ctx, const float* depth, int T, const float* poses,
+                        const bf_intrinsics* K, const bf_grid* grid, const bf_params* prm,
+                        bf_band** out);
+void bf_band_free(bf_band* band);
+
+/* Sizes: band voxels N, active bricks, candidate bricks evaluated. */
+bf_status bf_band_info(const bf_band* band, int64_t* n_vox, int32_t* n_bricks, int64_t* n_cand);
+
+/* Copy band arrays out (any argument may be NULL to skip it):
+ *   lin [N] int64 linear voxel index; tsdf [N] float metres; wcount [N]
+ *   int32 TSDF samples; bdry [N] uint8 (1 = in dB: fewer than 6 band
+ *   6-neighbours); brick_dir [nb^3] int32 rank or -1; mask [n_bricks][8]
+ *   uint64 band bit of local voxel l at bit (l & 63) of word l >> 6. */
+bf_status bf_export_band(bf_ctx* ctx, const bf_band* band, int64_t* lin, float* tsdf, int32_t* wcount,
+                         uint8_t* bdry, int32_t* brick_dir, uint64_t* mask);
+
+/* Depth-to-SDF observations and posterior assembly (Sec. 3.5 back-
+ * projection, projective SDF, linear row and noise equations; Sec. 3.6 Q0,
+ * precision and mean equations); Algorithm 1 steps 3-4.  For every valid
+ * pixel the ray segment [s_p - tau, s_p + tau] around the back-projected
+ * point is traversed voxel by voxel (3-D DDA, FP32 spec); each band voxel j
+ * it enters receives one row a = e_j with y = clamp(r.(p - x_j), -tau, tau)/h
+ * and precision w = h^2/sigma^2, sigma^2 = (sig_a + sig_b D^2)^2 + sig_pose^2
+ * + sig_model^2.  Then Q_jj = lambda deg_j + lambda_b [j in dB] + sum w and
+ * h_j = sum w y + lambda_b [j in dB] tsdf_j / h.  May be called several times
+ * (observations accumulate; the system is reassembled after each call). */
+bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* band, const float* depth, int T, const float* poses,
+                             const bf_intrinsics* K);
+
+/* Reset the accumulated observations of a band to zero. */
+bf_status bf_reset_observations(bf_ctx* ctx, bf_band* band);
+
+/* Copy the assembled system out ([N] float each; NULL skips):
+ * d = sum w, hdata = sum w y, qdiag = Q_jj, rhs = h_j. */
+bf_status bf_export_system(bf_ctx* ctx, const bf_band* band, float* d, float* hdata, float* qdiag, float* rhs);
+
+/* y = Q x for x, y [N] float (Sec. 3.6 precision equation; matrix-free
+ * 7-point stencil: (Qx)_j = Q_jj x_j - lambda sum_{6-nbrs k in B} x_k). */
+bf_status bf_spmv(bf_ctx* ctx, const bf_band* band, const float* x, float* y);
+
+/* MAP mean: solve Q mu = h by Jacobi-preconditioned CG (Sec. 3.6, MAP
+ * equation; Algorithm 1 step 5).  Stops when ||r||_2 <= rel_tol ||h||_2 on
+ * the recursive residual, then recomputes the true residual in FP64 and
+ * restarts from the current iterate (at most 3 times) if it misses.
+ *   mu [N] float (voxels); iters / rel_res (host, may be NULL) receive the
+ *   iteration count and the final true relative residual.
+ * Returns BF_NOT_CONVERGED after max_iter iterations (mu = last iterate),
+ * BF_BREAKDOWN on p.Qp <= 0 or a non-finite scalar, BF_ESTATE before
+ * bf_integrate_depth. */
+bf_status bf_solve_mean(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter, unsigned flags, float* mu,
+                        int* iters, double* rel_res);
+
+/* Probe estimate of diag(Q^-1) (Sec. 3.7, diag equation; Algorithm 1 step 6):
+ * s = (1/K) sum_k z_k (.) Q^-1 z_k with Rademacher probes z_k(j) = +1 if the
+ * top bit of SplitMix64(SplitMix64(seed) ^ k * 0xD1B54A32D192ED03 ^ lin_j)
+ * is 0, else -1 (lin_j the linear voxel index).  The K solves run as block
+ * PCG over rhs_block columns at a time (8, 16 or 32; 0 = library choice),
+ * every column to rel_tol as in bf_solve_mean.
+ *   s [N] float (voxels^2); total_iters (host, may be NULL) = sum over
+ *   probes of their iteration counts.
+ * Errors as bf_solve_mean; BF_EINVAL for K < 1 or an unsupported block. */
+bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* band, int K, uint64_t seed, double rel_tol, int max_iter,
+                               int rhs_block, unsigned flags, float* s, int* total_iters);
+
+/* Marching cubes on mu (Sec. 3.8; Algorithm 1 step 7): every cube of 8 band
+ * voxels, inside = mu < 0; per cube, polygons traced face by face
+ * (ambiguous faces separate the inside corners) and fan-triangulated from
+ * the lowest-numbered edge of each loop.  A vertex sits on each crossed
+ * grid edge at t = mu_a / (mu_a - mu_b) from its lower voxel a.  Vertices
+ * are ordered by (compact index of the lower voxel, axis), triangles by
+ * (compact index of the cube's lower corner voxel, loop order); triangle
+ * normals point to mu >= 0.  mu [N] float.  *nv, *nt (host) receive the
+ * counts; the mesh is kept in the context until bf_get_surface. */
+bf_status bf_extract_surface(bf_ctx* ctx, const bf_band* band, const float* mu, int64_t* nv, int64_t* nt);
+
+/* Copy the last extracted mesh: verts [nv][3] float metres, tris [nt][3] int32. */
+bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris);
+
+/* Next-best-view utilities (Sec. 3.8, NBV equation; Algorithm 1 step 8).
+ * For each candidate pose v (cand_poses [V][3][4], intrinsics K): the
+ * predicted depth of each pixel is the first outside->inside zero crossing
+ * of the trilinear interpolant of mu (march at h/2 from the grid entry, 10
+ * bisection steps, FP32 spec); the pixel then adds predicted precision
+ * dd_j = w(D) to the band voxels its DDA enters, as in bf_integrate_depth;
+ * U(v) = sum_{|mu_j| <= eps} s_j^2 dd_j / (1 + s_j dd_j), with s_j floored at
+ * 1/Q_jj.  mu [N] float (voxels), s [N] float (voxels^2); U [V] double
+ * (host or device); *best (host, may be NULL) = argmax, lowest index on ties. */
+bf_status bf_score_views(bf_ctx* ctx, const bf_band* band, const float* mu, const float* s,
+                         const float* cand_poses, int V, const bf_intrinsics* K, double eps, double* U, int* best);
+
+/* Kernel timing for roofline measurements: launches one kernel of the solver
+ * `reps` times back to back on the context stream between two CUDA events
+ * and returns the mean time per launch (ms).
+ *   BF_KERNEL_SPMV: the 7-point SpMV y = Q x over the band (bf_spmv's kernel);
+ *   BF_KERNEL_BLOCK_SPMV: the block-PCG kernel p <- r/qd + beta p, q = Q p over
+ *   R = 8, 16 or 32 columns (the probe solver's dominant kernel).
+ * Inputs are the library's own workspaces (their values are not preserved). */
+#define BF_KERNEL_SPMV 0
+#define BF_KERNEL_BLOCK_SPMV 1
+bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* band, int which, int R, int reps, double* ms_per_launch);
+
+/* Number of GPU kernels this library has run in this process (host launches
+ * plus the kernels executed inside its solver graphs); for accounting. */
+bf_status bf_launch_count(int64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFSDF_H */

@@ -1,0 +1,435 @@
+// C ABI of the posterior-solver library: argument checks, host/device
+// staging, context and workspace management.  The computation lives in the
+// other translation units.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
+
+bf_status bf_fail(bf_ctx* ctx, bf_status st, const char* what, const char* detail) {
+  if (ctx) {
+    ctx->err = what ? what : "";
+    if (detail) {
+      ctx->err += ": ";
+      ctx->err += detail;
+    }
+  }
+  return st;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bf_status dev_alloc(bf_ctx* ctx, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return bf_fail(ctx, BF_ENOMEM, "device allocation failed", cudaGetErrorString(e));
+  }
+  return BF_OK;
+}
+
+void dev_free(cudaStream_t s, void* p) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+void* ws_get(bf_ctx* ctx, int slot, size_t bytes, bf_status* st) {
+  Workspace& w = ctx->ws[slot];
+  if (bytes == 0) bytes = 16;
+  if (w.cap < bytes) {
+    if (w.p) cudaFreeAsync(w.p, ctx->stream);
+    w.p = nullptr;
+    w.cap = 0;
+    size_t cap = bytes + bytes / 8;
+    if (cudaMallocAsync(&w.p, cap, ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      *st = bf_fail(ctx, BF_ENOMEM, "workspace allocation failed");
+      return nullptr;
+    }
+    w.cap = cap;
+  }
+  *st = BF_OK;
+  return w.p;
+}
+
+namespace {
+
+// Device view of a caller array: the array itself if it is device memory,
+// else a staged copy in workspace slot `slot`.
+template <class T>
+bf_status stage_in(bf_ctx* ctx, const T* p, size_t count, int slot, const T** out) {
+  if (is_device_ptr(p)) {
+    *out = p;
+    return BF_OK;
+  }
+  bf_status st;
+  T* d = (T*)ws_get(ctx, slot, count * sizeof(T), &st);
+  if (st) return st;
+  BF_CK(cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  *out = d;
+  return BF_OK;
+}
+
+// Output target: the caller array if device memory, else a workspace buffer
+// that copy_out writes back.
+template <class T>
+bf_status stage_out(bf_ctx* ctx, T* p, size_t count, int slot, T** out, bool* host) {
+  *host = !is_device_ptr(p);
+  if (!*host) {
+    *out = p;
+    return BF_OK;
+  }
+  bf_status st;
+  *out = (T*)ws_get(ctx, slot, count * sizeof(T), &st);
+  return st;
+}
+
+template <class T>
+bf_status copy_out(bf_ctx* ctx, T* user, const T* dev, size_t count, bool host) {
+  if (!host) return BF_OK;
+  BF_CK(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+  BF_CK(cudaStreamSynchronize(ctx->stream));
+  return BF_OK;
+}
+
+__global__ void k_i32_to_i64(const int32_t* in, int64_t* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+__global__ void k_bdry(const uint8_t* info, uint8_t* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = info[i] >> 3;
+}
+
+__global__ void k_mask64(const MetaWord* meta, uint64_t* out, int64_t nwords64) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nwords64; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint64_t)meta[2 * i].bits | ((uint64_t)meta[2 * i + 1].bits << 32);
+}
+
+unsigned gsize(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+bool valid_intr(const bf_intrinsics* K) {
+  return K && K->W > 0 && K->H > 0 && K->W <= 16384 && K->H <= 16384 && K->fx > 0 && K->fy > 0 &&
+         std::isfinite(K->cx) && std::isfinite(K->cy);
+}
+
+Intr to_intr(const bf_intrinsics* K) {
+  Intr k;
+  k.fx = K->fx;
+  k.fy = K->fy;
+  k.cx = K->cx;
+  k.cy = K->cy;
+  k.W = K->W;
+  k.H = K->H;
+  return k;
+}
+
+}  // namespace
+
+extern "C" {
+
+bf_status bf_create(int device, void* stream, bf_ctx** out) {
+  if (!out) return BF_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return BF_ECUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return BF_ECUDA;
+  bf_ctx* ctx = new (std::nothrow) bf_ctx();
+  if (!ctx) return BF_ENOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (cudaMallocHost(&ctx->h_pinned, 64) != cudaSuccess) {
+    delete ctx;
+    return BF_ENOMEM;
+  }
+  *out = ctx;
+  return BF_OK;
+}
+
+void bf_destroy(bf_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& w : ctx->ws)
+    if (w.p) cudaFree(w.p);
+  if (ctx->mesh_v) cudaFree(ctx->mesh_v);
+  if (ctx->mesh_t) cudaFree(ctx->mesh_t);
+  if (ctx->mc_table) cudaFree(ctx->mc_table);
+  if (ctx->mc_ntri) cudaFree(ctx->mc_ntri);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+}
+
+const char* bf_last_error(const bf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+bf_status bf_set_stream(bf_ctx* ctx, void* stream) {
+  if (!ctx) return BF_EINVAL;
+  ctx->stream = (cudaStream_t)stream;
+  return BF_OK;
+}
+
+bf_status bf_build_band(bf_ctx* ctx, const float* depth, int T, const float* poses, const bf_intrinsics* K,
+                        const bf_grid* grid, const bf_params* prm, bf_band** out) {
+  if (!ctx || !out) return BF_EINVAL;
+  *out = nullptr;
+  if (!depth || !poses || !grid || !prm || T < 1 || !valid_intr(K))
+    return bf_fail(ctx, BF_EINVAL, "bf_build_band: null pointer, T < 1 or bad intrinsics");
+  if (grid->n < 8 || grid->n > 2048 || grid->n % 8 != 0 || !(grid->voxel > 0.0f))
+    return bf_fail(ctx, BF_EINVAL, "bf_build_band: n must be a multiple of 8 in [8, 2048], voxel > 0");
+  if (!(prm->band_vox > 0.0) || !(prm->trunc_vox > prm->band_vox) || prm->trunc_vox > 256.0 ||
+      !(prm->lambda >= 0.0) || !(prm->lambda_b >= 0.0))
+    return bf_fail(ctx, BF_EINVAL, "bf_build_band: need 0 < band_vox < trunc_vox <= 256, lambda, lambda_b >= 0");
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return bf_fail(ctx, BF_ECUDA, "cudaSetDevice");
+  const float *d_depth, *d_poses;
+  size_t npix = (size_t)T * K->H * K->W;
+  BF_TRY(stage_in(ctx, depth, npix, WS_STAGE0, &d_depth));
+  BF_TRY(stage_in(ctx, poses, (size_t)T * 12, WS_STAGE1, &d_poses));
+  return band_build(ctx, d_depth, T, d_poses, to_intr(K), *grid, *prm, out);
+}
+
+void bf_band_free(bf_band* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  solve_graph_free(b->sg);
+  block_graph_free(b->bg);
+  void* ptrs[] = {b->dir, b->bcoord, b->meta, b->off, b->nbr, b->lin, b->tsdf, b->wcount, b->info,
+                  b->d, b->hd, b->qd, b->rhs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete b;
+}
+
+bf_status bf_band_info(const bf_band* b, int64_t* n_vox, int32_t* n_bricks, int64_t* n_cand) {
+  if (!b) return BF_EINVAL;
+  if (n_vox) *n_vox = b->N;
+  if (n_bricks) *n_bricks = b->NB;
+  if (n_cand) *n_cand = b->ncand;
+  return BF_OK;
+}
+
+bf_status bf_export_band(bf_ctx* ctx, const bf_band* b, int64_t* lin, float* tsdf, int32_t* wcount, uint8_t* bdry,
+                         int32_t* brick_dir, uint64_t* mask) {
+  if (!ctx || !b) return BF_EINVAL;
+  cudaStream_t s = ctx->stream;
+  const int64_t N = b->N;
+  bool host;
+  if (lin && N) {
+    int64_t* d;
+    BF_TRY(stage_out(ctx, lin, N, WS_OUT0, &d, &host));
+    k_i32_to_i64<<<gsize(N), 256, 0, s>>>(b->lin, d, N); count_launch();
+    BF_TRY(copy_out(ctx, lin, d, N, host));
+  }
+  if (tsdf && N) {
+    if (is_device_ptr(tsdf)) BF_CK(cudaMemcpyAsync(tsdf, b->tsdf, N * 4, cudaMemcpyDeviceToDevice, s));
+    else BF_CK(cudaMemcpy(tsdf, b->tsdf, N * 4, cudaMemcpyDeviceToHost));
+  }
+  if (wcount && N) {
+    if (is_device_ptr(wcount)) BF_CK(cudaMemcpyAsync(wcount, b->wcount, N * 4, cudaMemcpyDeviceToDevice, s));
+    else BF_CK(cudaMemcpy(wcount, b->wcount, N * 4, cudaMemcpyDeviceToHost));
+  }
+  if (bdry && N) {
+    uint8_t* d;
+    BF_TRY(stage_out(ctx, bdry, N, WS_OUT0, &d, &host));
+    k_bdry<<<gsize(N), 256, 0, s>>>(b->info, d, N); count_launch();
+    BF_TRY(copy_out(ctx, bdry, d, N, host));
+  }
+  if (brick_dir) {
+    size_t nb3 = (size_t)b->nb * b->nb * b->nb;
+    if (is_device_ptr(brick_dir)) BF_CK(cudaMemcpyAsync(brick_dir, b->dir, nb3 * 4, cudaMemcpyDeviceToDevice, s));
+    else BF_CK(cudaMemcpy(brick_dir, b->dir, nb3 * 4, cudaMemcpyDeviceToHost));
+  }
+  if (mask && b->NB) {
+    uint64_t* d;
+    int64_t nw = (int64_t)b->NB * 8;
+    BF_TRY(stage_out(ctx, mask, nw, WS_OUT1, &d, &host));
+    k_mask64<<<gsize(nw), 256, 0, s>>>(b->meta, d, nw); count_launch();
+    BF_TRY(copy_out(ctx, mask, d, nw, host));
+  }
+  BF_CK(cudaGetLastError());
+  return BF_OK;
+}
+
+bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses,
+                             const bf_intrinsics* K) {
+  if (!ctx || !b) return BF_EINVAL;
+  if (!depth || !poses || T < 1 || !valid_intr(K))
+    return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth: null pointer, T < 1 or bad intrinsics");
+  const float *d_depth, *d_poses;
+  BF_TRY(stage_in(ctx, depth, (size_t)T * K->H * K->W, WS_STAGE0, &d_depth));
+  BF_TRY(stage_in(ctx, poses, (size_t)T * 12, WS_STAGE1, &d_poses));
+  return band_integrate(ctx, b, d_depth, T, d_poses, to_intr(K));
+}
+
+bf_status bf_reset_observations(bf_ctx* ctx, bf_band* b) {
+  if (!ctx || !b) return BF_EINVAL;
+  if (b->d) {
+    BF_CK(cudaMemsetAsync(b->d, 0, b->N * 4, ctx->stream));
+    BF_CK(cudaMemsetAsync(b->hd, 0, b->N * 4, ctx->stream));
+    return band_assemble(ctx, b);
+  }
+  return BF_OK;
+}
+
+bf_status bf_export_system(bf_ctx* ctx, const bf_band* b, float* d, float* hdata, float* qdiag, float* rhs) {
+  if (!ctx || !b) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_export_system: call bf_integrate_depth first");
+  const float* src[4] = {b->d, b->hd, b->qd, b->rhs};
+  float* dst[4] = {d, hdata, qdiag, rhs};
+  for (int k = 0; k < 4; ++k) {
+    if (!dst[k] || !b->N) continue;
+    if (is_device_ptr(dst[k])) BF_CK(cudaMemcpyAsync(dst[k], src[k], b->N * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    else {
+      BF_CK(cudaStreamSynchronize(ctx->stream));
+      BF_CK(cudaMemcpy(dst[k], src[k], b->N * 4, cudaMemcpyDeviceToHost));
+    }
+  }
+  return BF_OK;
+}
+
+bf_status bf_spmv(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
+  if (!ctx || !b || !x || !y) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_spmv: call bf_integrate_depth first");
+  const float* dx;
+  float* dy;
+  bool host;
+  BF_TRY(stage_in(ctx, x, b->N, WS_STAGE2, &dx));
+  BF_TRY(stage_out(ctx, y, b->N, WS_OUT0, &dy, &host));
+  BF_TRY(spmv_launch(ctx, b, dx, dy));
+  return copy_out(ctx, y, (const float*)dy, b->N, host);
+}
+
+bf_status bf_solve_mean(bf_ctx* ctx, bf_band* b, double rel_tol, int max_iter, unsigned flags, float* mu,
+                        int* iters, double* rel_res) {
+  if (!ctx || !b || !mu) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_solve_mean: call bf_integrate_depth first");
+  if (!(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
+    return bf_fail(ctx, BF_EINVAL, "bf_solve_mean: need 0 < rel_tol < 1 and 1 <= max_iter <= 1e7");
+  float* dmu;
+  bool host;
+  BF_TRY(stage_out(ctx, mu, b->N, WS_OUT0, &dmu, &host));
+  if ((flags & BF_SOLVE_WARM) && host && b->N)
+    BF_CK(cudaMemcpyAsync(dmu, mu, b->N * 4, cudaMemcpyHostToDevice, ctx->stream));
+  bf_status st = solve_mean_impl(ctx, b, rel_tol, max_iter, flags, dmu, iters, rel_res);
+  if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
+    bf_status c = copy_out(ctx, mu, (const float*)dmu, b->N, host);
+    if (c != BF_OK) return c;
+  }
+  return st;
+}
+
+bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, double rel_tol, int max_iter,
+                               int rhs_block, unsigned flags, float* s, int* total_iters) {
+  if (!ctx || !b || !s) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_estimate_variance: call bf_integrate_depth first");
+  if (K < 1 || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: need K >= 1, 0 < rel_tol < 1, 1 <= max_iter <= 1e7");
+  if (rhs_block != 0 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: rhs_block must be 0, 8, 16 or 32");
+  float* ds;
+  bool host;
+  BF_TRY(stage_out(ctx, s, b->N, WS_OUT1, &ds, &host));
+  bf_status st = variance_impl(ctx, b, K, seed, rel_tol, max_iter, rhs_block, flags, ds, total_iters);
+  if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
+    bf_status c = copy_out(ctx, s, (const float*)ds, b->N, host);
+    if (c != BF_OK) return c;
+  }
+  return st;
+}
+
+bf_status bf_extract_surface(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt) {
+  if (!ctx || !b || !mu || !nv || !nt) return BF_EINVAL;
+  const float* dmu;
+  BF_TRY(stage_in(ctx, mu, b->N, WS_STAGE2, &dmu));
+  return mc_impl(ctx, b, dmu, nv, nt);
+}
+
+bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris) {
+  if (!ctx) return BF_EINVAL;
+  if (verts && ctx->mesh_nv) {
+    cudaMemcpyKind k = is_device_ptr(verts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    BF_CK(cudaMemcpyAsync(verts, ctx->mesh_v, ctx->mesh_nv * 12, k, ctx->stream));
+  }
+  if (tris && ctx->mesh_nt) {
+    cudaMemcpyKind k = is_device_ptr(tris) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    BF_CK(cudaMemcpyAsync(tris, ctx->mesh_t, ctx->mesh_nt * 12, k, ctx->stream));
+  }
+  BF_CK(cudaStreamSynchronize(ctx->stream));
+  return BF_OK;
+}
+
+bf_status bf_score_views(bf_ctx* ctx, const bf_band* b, const float* mu, const float* s, const float* cand, int V,
+                         const bf_intrinsics* K, double eps, double* U, int* best) {
+  if (!ctx || !b || !mu || !s || !cand || !U || V < 1 || !valid_intr(K) || !(eps >= 0.0))
+    return bf_fail(ctx, BF_EINVAL, "bf_score_views: null pointer, V < 1, eps < 0 or bad intrinsics");
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_score_views: call bf_integrate_depth first");
+  const float *dmu, *ds, *dc;
+  BF_TRY(stage_in(ctx, mu, b->N, WS_STAGE2, &dmu));
+  BF_TRY(stage_in(ctx, s, b->N, WS_STAGE3, &ds));
+  BF_TRY(stage_in(ctx, cand, (size_t)V * 12, WS_STAGE1, &dc));
+  return nbv_impl(ctx, b, dmu, ds, dc, V, to_intr(K), eps, U, best);
+}
+
+bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms_per_launch) {
+  if (!ctx || !b || !ms_per_launch || reps < 1 || reps > 100000) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_bench_kernel: call bf_integrate_depth first");
+  if (b->N == 0) return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: empty band");
+  cudaStream_t s = ctx->stream;
+  if (which == BF_KERNEL_SPMV) {
+    bf_status st;
+    float* x = (float*)ws_get(ctx, WS_TMP0, (size_t)b->N * 4, &st);
+    if (st) return st;
+    float* y = (float*)ws_get(ctx, WS_TMP1, (size_t)b->N * 4, &st);
+    if (st) return st;
+    BF_CK(cudaMemsetAsync(x, 0, (size_t)b->N * 4, s));
+    cudaEvent_t e0, e1;
+    BF_CK(cudaEventCreate(&e0));
+    BF_CK(cudaEventCreate(&e1));
+    BF_CK(cudaEventRecord(e0, s));
+    for (int i = 0; i < reps; ++i) BF_TRY(spmv_launch(ctx, b, (i & 1) ? y : x, (i & 1) ? x : y));
+    BF_CK(cudaEventRecord(e1, s));
+    BF_CK(cudaEventSynchronize(e1));
+    float t = 0;
+    BF_CK(cudaEventElapsedTime(&t, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = t / reps;
+    return BF_OK;
+  }
+  if (which == BF_KERNEL_BLOCK_SPMV) return bench_block_spmv(ctx, b, R, reps, ms_per_launch);
+  return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: unknown kernel");
+}
+
+bf_status bf_launch_count(int64_t* n) {
+  if (!n) return BF_EINVAL;
+  *n = launch_total();
+  return BF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Internal declarations of the GB300 posterior-solver library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "bfsdf.h"
+
+// ------------------------------------------------------------- host side
+
+#define BF_CK(call)                                                                    \
+  do {                                                                                 \
+    cudaError_t e__ = (call);                                                          \
+    if (e__ != cudaSuccess) return bf_fail(ctx, BF_ECUDA, #call, cudaGetErrorString(e__)); \
+  } while (0)
+
+#define BF_TRY(call)                     \
+  do {                                   \
+    bf_status s__ = (call);              \
+    if (s__ != BF_OK) return s__;        \
+  } while (0)
+
+struct Workspace {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+enum { WS_STAGE0 = 0, WS_STAGE1, WS_STAGE2, WS_STAGE3, WS_OUT0, WS_OUT1, WS_TMP0, WS_TMP1, WS_TMP2, WS_TMP3,
+       WS_TMP4, WS_TMP5, WS_SCAN, WS_COUNT };
+
+struct SolveGraph;  // solve.cu
+struct BlockGraph;  // block.cu
+
+struct bf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  Workspace ws[WS_COUNT];
+  int32_t* h_pinned = nullptr;  // small pinned scratch for scalars read back
+  // last extracted mesh
+  float* mesh_v = nullptr;
+  int32_t* mesh_t = nullptr;
+  int64_t mesh_nv = 0, mesh_nt = 0;
+  size_t mesh_vcap = 0, mesh_tcap = 0;
+  int8_t* mc_table = nullptr;   // device [256][16][3] edge triples, -1 padded
+  int8_t* mc_ntri = nullptr;    // device [256]
+};
+
+// Per-brick lookup entry: band bits of 32 local voxels and the compact index
+// of the first of them (brick offset + band voxels in earlier words).
+struct __align__(8) MetaWord {
+  uint32_t bits;
+  int32_t base;
+};
+
+struct bf_band {
+  bf_grid grid;
+  bf_params prm;
+  int nb = 0;
+  int32_t NB = 0;
+  int64_t N = 0;
+  int64_t ncand = 0;
+  cudaStream_t stream = nullptr;  // stream the arrays were allocated on
+  // directory and per-brick data
+  int32_t* dir = nullptr;     // [nb^3] rank or -1
+  int32_t* bcoord = nullptr;  // [NB][4] (bi, bj, bk, 0)
+  MetaWord* meta = nullptr;   // [NB][16]
+  int32_t* off = nullptr;     // [NB+1]
+  int32_t* nbr = nullptr;     // [NB][6]  -x,+x,-y,+y,-z,+z
+  // per-voxel data
+  int32_t* lin = nullptr;     // [N]
+  float* tsdf = nullptr;      // [N] metres
+  int32_t* wcount = nullptr;  // [N]
+  uint8_t* info = nullptr;    // [N] deg | bdry << 3
+  float* d = nullptr;         // [N] sum w
+  float* hd = nullptr;        // [N] sum w y
+  float* qd = nullptr;        // [N] Q_jj
+  float* rhs = nullptr;       // [N] h_j
+  bool integrated = false;
+  // solver state (lazily allocated)
+  SolveGraph* sg = nullptr;
+  BlockGraph* bg = nullptr;
+};
+
+// POD view of a band passed to kernels.
+struct BandView {
+  int n, nb, NB, N;
+  float h, o0, o1, o2;
+  const int32_t* dir;
+  const MetaWord* meta;
+  const int32_t* off;
+  const int32_t* nbr;
+  const int32_t* bcoord;
+  const int32_t* lin;
+};
+
+struct Intr {
+  float fx, fy, cx, cy;
+  int W, H;
+};
+
+bf_status bf_fail(bf_ctx* ctx, bf_status st, const char* what, const char* detail = nullptr);
+void* ws_get(bf_ctx* ctx, int slot, size_t bytes, bf_status* st);
+bool is_device_ptr(const void* p);
+BandView band_view(const bf_band* b);
+bf_status dev_alloc(bf_ctx* ctx, void** p, size_t bytes);
+template <class T>
+inline bf_status dev_alloc_t(bf_ctx* ctx, T** p, size_t count) {
+  return dev_alloc(ctx, (void**)p, count * sizeof(T));
+}
+void dev_free(cudaStream_t s, void* p);
+
+// Exclusive prefix sum of n int32 values (in and out may alias); *total
+// (device, may be null) receives the sum.
+bf_status scan_i32(bf_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, int32_t* total);
+
+// Module entry points (host side of each .cu file).
+bf_status band_build(bf_ctx* ctx, const float* depth, int T, const float* poses, const Intr& K, const bf_grid& g,
+                     const bf_params& p, bf_band** out);
+bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses, const Intr& K);
+bf_status band_assemble(bf_ctx* ctx, bf_band* b);
+bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
+bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,
+                          double* relres);
+bf_status variance_impl(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, double tol, int max_iter, int R,
+                        unsigned flags, float* s, int* total_iters);
+bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms);
+void solve_graph_free(SolveGraph* g);
+void block_graph_free(BlockGraph* g);
+bf_status mc_impl(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt);
+bf_status nbv_impl(bf_ctx* ctx, const bf_band* b, const float* mu, const float* s, const float* cand, int V,
+                   const Intr& K, double eps, double* U, int* best);
+
+// ---------------------------------------------------------- device side
+
+#ifdef __CUDACC__
+
+// FP32 specification arithmetic: each operation rounded separately (no FMA
+// contraction), so discrete decisions are reproducible bit for bit.
+__device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float f_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float f_div(float a, float b) { return __fdiv_rn(a, b); }
+
+struct Pose {
+  float R[9];
+  float C[3];
+};
+
+__device__ __forceinline__ Pose load_pose(const float* __restrict__ P) {
+  Pose q;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) q.R[3 * a + b] = P[4 * a + b];
+    q.C[a] = P[4 * a + 3];
+  }
+  return q;
+}
+
+__device__ __forceinline__ bool depth_ok(float D) { return D > 0.0f && D < __int_as_float(0x7f800000); }
+
+// voxel centre coordinate along one axis: org + (i + 1/2) h
+__device__ __forceinline__ float vox_c(float org, float h, int i) {
+  return f_add(org, f_mul(f_add((float)i, 0.5f), h));
+}
+
+// pixel ray: dw = R K^-1 (px+1/2, py+1/2, 1), nrm = |K^-1 u|, r = dw / nrm
+struct Ray {
+  float dw[3], r[3], nrm;
+};
+
+__device__ __forceinline__ Ray pixel_ray(const Pose& P, int px, int py, const Intr& K) {
+  Ray q;
+  float a = f_div(f_sub(f_add((float)px, 0.5f), K.cx), K.fx);
+  float b = f_div(f_sub(f_add((float)py, 0.5f), K.cy), K.fy);
+  q.nrm = __fsqrt_rn(f_add(f_add(f_mul(a, a), f_mul(b, b)), 1.0f));
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    q.dw[k] = f_add(f_add(f_mul(P.R[3 * k], a), f_mul(P.R[3 * k + 1], b)), P.R[3 * k + 2]);
+    q.r[k] = f_div(q.dw[k], q.nrm);
+  }
+  return q;
+}
+
+// compact index of voxel (i,j,k) or -1 if outside the band
+__device__ __forceinline__ int band_lookup(const BandView& B, int i, int j, int k) {
+  if ((unsigned)i >= (unsigned)B.n || (unsigned)j >= (unsigned)B.n || (unsigned)k >= (unsigned)B.n) return -1;
+  int r = __ldg(B.dir + ((i >> 3) + B.nb * ((j >> 3) + B.nb * (k >> 3))));
+  if (r < 0) return -1;
+  int l = (i & 7) + 8 * (j & 7) + 64 * (k & 7);
+  MetaWord m = B.meta[16 * r + (l >> 5)];
+  uint32_t bit = 1u << (l & 31);
+  if (!(m.bits & bit)) return -1;
+  return m.base + __popc(m.bits & (bit - 1u));
+}
+
+// FP32-spec 3-D DDA over s in [sp - tau, sp + tau]; calls f(i, j, k) for each
+// voxel entered (ties broken x < y < z), at most max_steps voxels.
+template <class F>
+__device__ __forceinline__ void dda_walk(const float C[3], const float r[3], float sp, float tau, float h,
+                                         const float org[3], int max_steps, F&& f) {
+  float s0 = f_sub(sp, tau);
+  if (s0 < 0.0f) s0 = 0.0f;
+  float s1 = f_add(sp, tau);
+  float P0[3], tmax[3], tdel[3];
+  int idx[3], step[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    P0[k] = f_add(C[k], f_mul(s0, r[k]));
+    float g = f_div(f_sub(P0[k], org[k]), h);
+    if (!(fabsf(g) < 1.0e6f)) return;
+    idx[k] = (int)floorf(g);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    if (r[k] > 0.0f) {
+      step[k] = 1;
+      tdel[k] = f_div(h, r[k]);
+      float bnd = f_add(org[k], f_mul((float)(idx[k] + 1), h));
+      tmax[k] = f_add(s0, f_div(f_sub(bnd, P0[k]), r[k]));
+    } else if (r[k] < 0.0f) {
+      step[k] = -1;
+      tdel[k] = f_div(h, -r[k]);
+      float bnd = f_add(org[k], f_mul((float)idx[k], h));
+      tmax[k] = f_add(s0, f_div(f_sub(bnd, P0[k]), r[k]));
+    } else {
+      step[k] = 0;
+      tdel[k] = __int_as_float(0x7f800000);
+      tmax[k] = __int_as_float(0x7f800000);
+    }
+  }
+  for (int it = 0; it < max_steps; ++it) {
+    f(idx[0], idx[1], idx[2]);
+    int a = (tmax[0] <= tmax[1] && tmax[0] <= tmax[2]) ? 0 : (tmax[1] <= tmax[2] ? 1 : 2);
+    float ta = a == 0 ? tmax[0] : (a == 1 ? tmax[1] : tmax[2]);
+    if (ta > s1) break;
+    if (a == 0) { idx[0] += step[0]; tmax[0] = f_add(tmax[0], tdel[0]); }
+    else if (a == 1) { idx[1] += step[1]; tmax[1] = f_add(tmax[1], tdel[1]); }
+    else { idx[2] += step[2]; tmax[2] = f_add(tmax[2], tdel[2]); }
+  }
+}
+
+__host__ __device__ inline int dda_max_steps(double band_vox) {
+  return 3 * (int)ceil(2.0 * band_vox) + 12;
+}
+
+__host__ __device__ inline int brick_radius(double trunc_vox) {
+  return (int)floor((1.25 * trunc_vox + 2.0) / 8.0) + 1;
+}
+
+#endif  // __CUDACC__
+
+// Kernels launched by this library (host launches plus graph-body kernel
+// executions), process-wide.
+void count_launch(int64_t n = 1);
+int64_t launch_total();

@@ -136,41 +136,50 @@ def max_over_ranks(world, v: float) -> float:
 
 # ----------------------------------------------------------------- oracle
 
-def oracle_sample(w, tol, K, budget_s):
+def oracle_system(w):
+    """Untimed set-up of the oracle's posterior system for workload w."""
+    import oracle
+    b = oracle.build_band_w(w)
+    d, hd, _ = oracle.integrate_w(b, w)
+    qd, rhs = oracle.assemble(b, d, hd, w.lam, w.lam_b)
+    return b, qd, rhs
+
+
+def oracle_sample(w, system, tol, K, budget_s, k0=0):
     """Time the oracle's posterior solve on a bounded sample: the mean solve
     plus as many of the K probe solves as fit in budget_s; extrapolated
     linearly to K probes."""
     import oracle
+    b, qd, rhs = system
     cores = len(os.sched_getaffinity(0))
-    b = oracle.build_band_w(w)
-    d, hd, _ = oracle.integrate_w(b, w)
-    qd, rhs = oracle.assemble(b, d, hd, w.lam, w.lam_b)
     t0 = time.perf_counter()
     oracle.pcg(b, w.lam, qd, rhs, tol=tol)
     t_mean = time.perf_counter() - t0
     t1 = time.perf_counter()
     k = 0
     while k < K and (k < 1 or time.perf_counter() - t1 < budget_s):
-        oracle.hutchinson(b, w.lam, qd, 1, w.seed, tol=tol, k0=k)
+        oracle.hutchinson(b, w.lam, qd, 1, w.seed, tol=tol, k0=(k0 + k) % K)
         k += 1
     t_probe = (time.perf_counter() - t1) / k
     est = t_mean + K * t_probe
     sample = (f"{w.name}: oracle mean solve + {k} of {K} probe solves at rel_tol {tol:g} on N={b.N} band "
-              f"voxels, FP64 CSR PCG; time extrapolated linearly to {K} probes")
+              f"voxels (FP64 CSR PCG, OpenMP over {cores} threads); time extrapolated linearly to {K} probes")
     return est, cores, sample, k
 
 
 def run_reference(args, world, rank):
+    """The CPU oracle as the reference arm: each step times a bounded sample
+    of the posterior solve on the host cores (rank 0 only)."""
     if rank != 0:
         return
     import synth
     w = synth.make_workload(args.workload)
+    system = oracle_system(w)
     vals = []
-    k_used = 0
     cores, sample = 1, ""
+    budget = max(1.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
     for i in range(args.warmup + args.steps):
-        budget = max(2.0, args.cpu_seconds / max(args.steps, 1))
-        est, cores, sample, k_used = oracle_sample(w, args.tol, args.K, budget)
+        est, cores, sample, _ = oracle_sample(w, system, args.tol, args.K, budget, k0=i)
         if i >= args.warmup:
             vals.append(est)
     v = statistics.mean(vals)
@@ -315,7 +324,7 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        est, cores, sample, k = oracle_sample(w, args.tol, args.K, args.cpu_seconds)
+        est, cores, sample, k = oracle_sample(w, oracle_system(w), args.tol, args.K, args.cpu_seconds)
         cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:

@@ -218,7 +218,7 @@ def run_ours(args, world, rank, local):
             return _step()
 
     def _step():
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         ev[0].record(stream)
         band = ctx.build_band_w(w, depth, poses)
         ev[1].record(stream)
@@ -227,14 +227,15 @@ def run_ours(args, world, rank, local):
         mu = torch.empty(band.N, device=dev)
         s = torch.empty(band.N, device=dev)
         im = band.solve_mean(mu, rel_tol=args.tol)
-        iv = band.estimate_variance(s, K=args.K, seed=0, rel_tol=args.tol, rhs_block=R)
         ev[3].record(stream)
-        V, F = band.extract_surface(mu, device=dev)
+        iv = band.estimate_variance(s, K=args.K, seed=0, rel_tol=args.tol, rhs_block=R)
         ev[4].record(stream)
-        U, best = band.score_views(mu, s, cand, w.cand_intr)
+        V, F = band.extract_surface(mu, device=dev)
         ev[5].record(stream)
+        U, best = band.score_views(mu, s, cand, w.cand_intr)
+        ev[6].record(stream)
         stream.synchronize()
-        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(6)]
         info = dict(N=band.N, NB=band.NB, mean_iters=im.iters, var_iters=iv.iters, tris=int(F.shape[0]),
                     best_view=best)
         return band, t, info
@@ -266,7 +267,7 @@ def run_ours(args, world, rank, local):
     launches = (bfsdf.launch_count() - l0) // max(args.steps, 1)
     clocks = clk.stop()
 
-    post = [t[2] for t in times]            # solve_mean + estimate_variance (ms)
+    post = [t[2] + t[3] for t in times]     # solve_mean + estimate_variance (ms)
     stepms = [sum(t) for t in times]
     post_s = max_over_ranks(world, statistics.mean(post) / 1e3)
     step_s = max_over_ranks(world, statistics.mean(stepms) / 1e3)
@@ -278,18 +279,26 @@ def run_ours(args, world, rank, local):
     band.integrate_depth(depth, poses, w.intr)
     s = torch.empty(band.N, device=dev)
     band.estimate_variance(s, K=R, seed=0, rel_tol=args.tol, rhs_block=R)
-    ms_blk = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_SPMV, R=R, reps=50)
+    ms_upd = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_UPDATE, R=R, reps=50)
+    ms_spmm = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_SPMM, R=R, reps=50)
+    ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R, reps=50)
     N, NB = band.N, band.NB
-    # algorithmic bytes: per (voxel, column) r, p_in read + p_out, q written (16 B);
-    # per voxel qd (4 B); per brick 16 lookup words (128 B) + 6 neighbour ranks (24 B)
-    bytes_blk = N * R * 16 + N * 4 + NB * (128 + 24)
+    # algorithmic bytes of the probe solver's passes (per voxel row of R columns):
+    # update pass: r, w, s, p, x read, p, s, x, r, u written (40 B per column),
+    # 1/Q_jj read (4 B); SpMM pass: u read, w written (8 B per column), six
+    # neighbour indices and Q_jj read (28 B)
+    bytes_upd = N * (R * 40 + 4)
+    bytes_spmm = N * (R * 8 + 28)
     ms_spmv = band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=200)
     bytes_spmv = N * 12 + NB * (128 + 24)   # x, qd read, y written; brick metadata
-    achieved = bytes_blk / (ms_blk * 1e-3) / 1e9
-    roof = {"kernel": "k_blk_spmv<%d> (block-PCG p-update + 7-point SpMM + p.q)" % R, "bound": "hbm",
+    achieved = bytes_upd / (ms_upd * 1e-3) / 1e9
+    roof = {"kernel": "k_blk_upd<%d> (probe-solver vector-update pass, the dominant kernel)" % R, "bound": "hbm",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-            "peak_kind": peak_kind, "traffic": None, "bytes_per_launch": bytes_blk,
-            "ms_per_launch": round(ms_blk, 5)}
+            "peak_kind": peak_kind, "traffic": None, "bytes_per_launch": bytes_upd,
+            "ms_per_launch": round(ms_upd, 5),
+            "spmm_pass": {"kernel": "k_blk_spmm<%d>" % R, "ms_per_launch": round(ms_spmm, 5),
+                          "achieved": round(bytes_spmm / (ms_spmm * 1e-3) / 1e9, 1), "bytes_per_launch": bytes_spmm},
+            "iteration": {"ms": round(ms_iter, 5), "achieved": round((bytes_upd + bytes_spmm) / (ms_iter * 1e-3) / 1e9, 1)}}
     spmv = {"kernel": "k_brick (7-point SpMV, single RHS)", "achieved": round(bytes_spmv / (ms_spmv * 1e-3) / 1e9, 1),
             "ms_per_launch": round(ms_spmv, 5), "bytes_per_launch": bytes_spmv,
             "note": "single-RHS vectors of this workload are L2-resident (%.1f MB)" % (N * 12 / 1e6)}
@@ -338,8 +347,8 @@ def run_ours(args, world, rank, local):
                            "l2": "512 MB buffer written between timed steps",
                            "parallelism": f"replicas x{world}"},
                 "breakdown_ms": {"build_band": mean_t[0], "integrate_depth": mean_t[1],
-                                 "posterior_solve": mean_t[2], "extract_surface": mean_t[3],
-                                 "score_views": mean_t[4]},
+                                 "solve_mean": mean_t[2], "estimate_variance": mean_t[3],
+                                 "extract_surface": mean_t[4], "score_views": mean_t[5]},
                 "iters": {"mean": info["mean_iters"], "variance_total": info["var_iters"]},
                 "roofline": roof, "spmv": spmv, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "wall_s": round(wall, 3)}

@@ -191,15 +191,19 @@ bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris);
 bf_status bf_score_views(bf_ctx* ctx, const bf_band* band, const float* mu, const float* s,
                          const float* cand_poses, int V, const bf_intrinsics* K, double eps, double* U, int* best);
 
-/* Kernel timing for roofline measurements: launches one kernel of the solver
+/* Kernel timing for roofline measurements: launches kernels of the solver
  * `reps` times back to back on the context stream between two CUDA events
- * and returns the mean time per launch (ms).
+ * and returns the mean time per repetition (ms).
  *   BF_KERNEL_SPMV: the 7-point SpMV y = Q x over the band (bf_spmv's kernel);
- *   BF_KERNEL_BLOCK_SPMV: the block-PCG kernel p <- r/qd + beta p, q = Q p over
- *   R = 8, 16 or 32 columns (the probe solver's dominant kernel).
+ *   BF_KERNEL_BLOCK_ITER: one probe-solver iteration over R = 8, 16 or 32
+ *     columns (BF_KERNEL_BLOCK_UPDATE followed by BF_KERNEL_BLOCK_SPMM);
+ *   BF_KERNEL_BLOCK_UPDATE: its streaming vector-update pass;
+ *   BF_KERNEL_BLOCK_SPMM: its w = Q u pass.
  * Inputs are the library's own workspaces (their values are not preserved). */
 #define BF_KERNEL_SPMV 0
-#define BF_KERNEL_BLOCK_SPMV 1
+#define BF_KERNEL_BLOCK_ITER 1
+#define BF_KERNEL_BLOCK_UPDATE 2
+#define BF_KERNEL_BLOCK_SPMM 3
 bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* band, int which, int R, int reps, double* ms_per_launch);
 
 /* Number of GPU kernels this library has run in this process (host launches

@@ -33,7 +33,9 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_spmv", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
             "bf_score_views", "bf_bench_kernel", "bf_launch_count"]
 BF_KERNEL_SPMV = 0
-BF_KERNEL_BLOCK_SPMV = 1
+BF_KERNEL_BLOCK_ITER = 1
+BF_KERNEL_BLOCK_UPDATE = 2
+BF_KERNEL_BLOCK_SPMM = 3
 
 
 class BfError(RuntimeError):

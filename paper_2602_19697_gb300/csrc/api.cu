@@ -183,6 +183,8 @@ void bf_destroy(bf_ctx* ctx) {
   if (ctx->mesh_t) cudaFree(ctx->mesh_t);
   if (ctx->mc_table) cudaFree(ctx->mc_table);
   if (ctx->mc_ntri) cudaFree(ctx->mc_ntri);
+  for (BlockGraph* g : ctx->blk) block_graph_free(g);
+  for (SolveGraph* g : ctx->sgl) solve_graph_free(g);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   delete ctx;
 }
@@ -217,10 +219,8 @@ bf_status bf_build_band(bf_ctx* ctx, const float* depth, int T, const float* pos
 void bf_band_free(bf_band* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
-  solve_graph_free(b->sg);
-  block_graph_free(b->bg);
   void* ptrs[] = {b->dir, b->bcoord, b->meta, b->off, b->nbr, b->lin, b->tsdf, b->wcount, b->info,
-                  b->d, b->hd, b->qd, b->rhs};
+                  b->d, b->hd, b->qd, b->rhs, b->nb6};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -422,7 +422,9 @@ bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, d
     *ms_per_launch = t / reps;
     return BF_OK;
   }
-  if (which == BF_KERNEL_BLOCK_SPMV) return bench_block_spmv(ctx, b, R, reps, ms_per_launch);
+  if (which == BF_KERNEL_BLOCK_ITER) return bench_block_spmv(ctx, b, 0, R, reps, ms_per_launch);
+  if (which == BF_KERNEL_BLOCK_UPDATE) return bench_block_spmv(ctx, b, 1, R, reps, ms_per_launch);
+  if (which == BF_KERNEL_BLOCK_SPMM) return bench_block_spmv(ctx, b, 2, R, reps, ms_per_launch);
   return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: unknown kernel");
 }
 

@@ -1,18 +1,38 @@
 // Probe estimate of diag(Q^-1) (Sec. 3.7 diag equation; Algorithm 1 step 6)
 // with the K probe solves batched as block PCG over R right-hand sides.
 //
-// Layout: block vectors are [N][R] float (row = one band voxel, R columns
-// contiguous), the probes Z are [N][R] bf16 (+-1 is exact in bf16).  Each
-// column is an independent Jacobi-PCG with its own alpha, beta and stop
-// flag; converged columns are frozen (alpha = 0).  Per iteration:
-//   A  k_blk_spmv: per brick (CTA-strided), per 4-column chunk: p <- r/qd +
-//      beta p staged with the halo in a 10^3 float4 shared tile, q = Q p,
-//      partial p.q per column; the last CTA sets alpha per column.
-//   B  k_blk_update: x += alpha p, r -= alpha q, partial r.(r/qd), r.r per
-//      column; the last CTA sets beta, stop flags and the iteration count.
-// The loop runs as a CUDA-graph WHILE node as in the single-RHS solver.
-// After convergence the true residual (FP64 accumulation) is recomputed per
-// column and the columns that miss restart; then s += z (.) x.
+// Layout: block vectors are [N][R] float (one row per band voxel, the R
+// probe columns contiguous, so a warp reads a row as one 128-byte line);
+// probes Z are [N][R] bf16 (+-1 is exact in bf16).  Every column is an
+// independent Jacobi-PCG with its own scalars and stop flag; converged
+// columns are frozen (alpha = beta = 0).
+//
+// Iteration: the single-reduction form of PCG (Chronopoulos & Gear, 1989):
+//   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
+//   u = r / qd,      w = Q u,        gamma = r.u,   delta = w.u,  r.r
+// with s = Q p carried by recurrence, so Q is applied once per iteration, to
+// u.  Two passes per iteration:
+//   k_blk_upd   streaming, float4 over 4 columns, in place: p, s, x, r, u and
+//               the partial sums of r.u and r.r (no neighbour access);
+//   k_blk_spmm  w = Q u: a warp takes 32/R rows at a time (lane = column),
+//               reading u at the six neighbours through a per-voxel
+//               neighbour table that each warp loads for 32 rows at once and
+//               broadcasts by shuffles; partial sums of w.u.
+// Partial sums are FP32 products summed over chunks of 8, accumulated in
+// FP64, reduced per CTA and then by the last CTA in a fixed order
+// (deterministic), which updates per column
+//   beta' = gamma'/gamma,  alpha' = gamma' / (delta' - beta' gamma'/alpha)
+// and the stop flags.  The iteration loop is a CUDA-graph WHILE node.
+//
+// Refinement: FP64 master iterates x64 per column; k_blk_outer computes the
+// true residual z - Q x64 in FP64, the FP32 solve reduces it by a factor
+// eta, x64 += x, until every column meets the tolerance.
+//
+// The solver (workspaces, state, graph) belongs to the context, one per
+// block width R: kernels read band pointers and sizes from a device-resident
+// argument block, so the captured graph serves every band.
+#include <cstring>
+
 #include "internal.cuh"
 
 #include <cuda_bf16.h>
@@ -20,17 +40,40 @@
 namespace {
 
 constexpr int MAXR = 32;
-constexpr int BT = 128;
-constexpr int UT = 256;
+constexpr int CT = 512;   // threads per CTA of the row kernels
+// smallest relative residual reduction asked of one FP32 correction solve
+// (the FP32 recursive residual keeps falling below the true one's floor)
+constexpr double ETA_MIN = 1e-7;
+constexpr int NCTA = 152 * 2;
 
 struct BlkState {
-  double rho[MAXR], pq[MAXR], alpha[MAXR], beta[MAXR], rr[MAXR], bb[MAXR], tol2[MAXR];  // inner PCG per column
+  double alpha[MAXR], beta[MAXR], gamma[MAXR], rr[MAXR], bb[MAXR], tol2[MAXR];
   double rr0[MAXR], bb0[MAXR];  // true residual and |z|^2 per column
   int done[MAXR], iters[MAXR];
   double tol0;
   int iter, max_iter, all_done, status, ncols;
-  unsigned int cntA, cntB, cntR, guard;
+  int first;  // the next pass-2 finalize starts a correction solve
+  unsigned int cnt, guard;
   unsigned int nexec;  // graph-body kernels executed (for launch accounting)
+};
+
+// Everything a kernel needs about the band and the workspaces.
+struct BlkArgs {
+  int N;
+  float lam;
+  const int32_t* nb6;  // [N][6] face-neighbour indices, -1 outside the band
+  const float* qd;     // [N] Q_jj
+  float* iq;           // [N] 1 / Q_jj
+  float* r[2];         // only [0] is used by the two-pass iteration
+  float* w[2];
+  float* s[2];
+  float* p;
+  float* x;            // FP32 correction
+  float* u;            // M^-1 r
+  double* x64;         // FP64 master iterates
+  const __nv_bfloat16* Z;
+  double* part;        // [3][R][NCTA]
+  double* part1;       // [2][R][NCTA] pass-1 partials
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -38,39 +81,6 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
-__device__ __forceinline__ float4 operator+(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
-__device__ __forceinline__ float4 operator-(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-__device__ __forceinline__ float4 operator*(float4 a, float4 b) { return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w); }
-
-// sum over the threads of a CTA that share (threadIdx.x % G), per component;
-// result in out[g][k] (shared), valid after the call
-template <int NV, int NW>
-__device__ __forceinline__ void group_sum(double (&v)[NV], int G, double (*out)[NV]) {
-  __shared__ double sh[NW][8][NV];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double x = v[k];
-    for (int o = 16; o >= G; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    v[k] = x;
-  }
-  if (lane < G) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sh[w][lane][k] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < G) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0;
-      for (int q = 0; q < NW; ++q) s += sh[q][threadIdx.x][k];
-      out[threadIdx.x][k] = s;
-    }
-  }
-  __syncthreads();
 }
 
 __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
@@ -101,401 +111,342 @@ __device__ __forceinline__ void sum_partials(const double* part, int R, int nblk
   __syncthreads();
 }
 
-// halo slot q in [0, 384): face q/64, (u, v) = (q & 7, (q >> 3) & 7) over the
-// face's other two axes; returns the neighbour's compact index (or -1) and
-// the position in the 10^3 tile
-__device__ __forceinline__ void halo_slot(const MetaWord (*sm)[16], int q, int* hidx, int* htile) {
-  int f = q >> 6, u = q & 7, v = (q >> 3) & 7;
-  int a = f >> 1, side = f & 1;
-  int lc[3], tc[3];
-  int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
-  lc[a] = side ? 0 : 7;
-  tc[a] = side ? 9 : 0;
-  lc[o1] = u;
-  lc[o2] = v;
-  tc[o1] = u + 1;
-  tc[o2] = v + 1;
-  int l = lc[0] + 8 * lc[1] + 64 * lc[2];
-  MetaWord m = sm[1 + f][l >> 5];
-  uint32_t bit = 1u << (l & 31);
-  *hidx = (m.bits & bit) ? m.base + __popc(m.bits & (bit - 1u)) : -1;
-  *htile = tc[0] + 10 * tc[1] + 100 * tc[2];
-}
-
-// One CTA per brick (CTA-strided), 4 columns per pass through a float4 tile:
-// p <- r/qd + beta p (own voxels and halo), q = Q p, partial p.q per column.
-template <int R>
-__global__ void __launch_bounds__(BT) k_blk_spmv(BandView B, float lam, const float* __restrict__ qd,
-                                                 const float* __restrict__ pin, const float* __restrict__ rin,
-                                                 float* __restrict__ pout, float* __restrict__ yout, double* part,
-                                                 BlkState* st, cudaGraphConditionalHandle handle) {
-  constexpr int NCH = R / 4;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->nexec += 2;  // this kernel and the update that follows it
-    unsigned g = atomicAdd(&st->guard, 1u);
-    if (st->all_done || g > 2u * (unsigned)st->max_iter + 64u) {
-      if (!st->all_done) { st->status = 1; st->all_done = 1; }
-      cudaGraphSetConditional(handle, 0);
-    }
-  }
-  if (st->all_done) return;
-  __shared__ float4 tile[1000];
-  __shared__ MetaWord sm[7][16];
-  __shared__ float hq[384];
-  __shared__ float sbeta[R];
-  __shared__ double red[4][4];
-  const int tid = threadIdx.x;
-  if (tid < R) sbeta[tid] = (float)st->beta[tid];
-  double acc[NCH][4];
+// per-column CTA sums of NV values held one column per lane (lane % R) ->
+// part[k][c][blockIdx.x]
+template <int R, int NV>
+__device__ __forceinline__ void column_partials(double (&v)[NV], double* part) {
+  __shared__ double sh[CT / 32][NV][MAXR];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int ch = 0; ch < NCH; ++ch)
+  for (int k = 0; k < NV; ++k)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[ch][k] = 0.0;
-
-  for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
-    __syncthreads();
-    if (tid < 7 * 16) {
-      int which = tid >> 4, w = tid & 15;
-      int r = which == 0 ? b : __ldg(B.nbr + 6 * b + which - 1);
-      MetaWord m;
-      m.bits = 0;
-      m.base = 0;
-      if (r >= 0) m = B.meta[16 * r + w];
-      sm[which][w] = m;
-    }
-    __syncthreads();
-    int idx[4], hidx[3], htile[3];
-    float qv[4];
+    for (int o = 16; o >= R; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane < R) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      int l = tid + BT * s;
-      MetaWord m = sm[0][l >> 5];
-      uint32_t bit = 1u << (l & 31);
-      idx[s] = (m.bits & bit) ? m.base + __popc(m.bits & (bit - 1u)) : -1;
-      qv[s] = idx[s] >= 0 ? __ldg(qd + idx[s]) : 1.0f;
-    }
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      int q = tid + BT * s;
-      halo_slot(sm, q, &hidx[s], &htile[s]);
-      hq[q] = hidx[s] >= 0 ? __ldg(qd + hidx[s]) : 1.0f;
-    }
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch) {
-      const float4 bet = make_float4(sbeta[4 * ch], sbeta[4 * ch + 1], sbeta[4 * ch + 2], sbeta[4 * ch + 3]);
-      float4 val[4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        float4 v = f4(0.0f);
-        if (idx[s] >= 0) {
-          const size_t o = (size_t)idx[s] * R + 4 * ch;
-          float4 rr = __ldg((const float4*)(rin + o));
-          float4 pp = __ldg((const float4*)(pin + o));
-          v = rr * f4(1.0f / qv[s]) + bet * pp;
-        }
-        val[s] = v;
-        int l = tid + BT * s;
-        tile[(l & 7) + 1 + 10 * (((l >> 3) & 7) + 1) + 100 * ((l >> 6) + 1)] = v;
-      }
-#pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        float4 v = f4(0.0f);
-        if (hidx[s] >= 0) {
-          const size_t o = (size_t)hidx[s] * R + 4 * ch;
-          float4 rr = __ldg((const float4*)(rin + o));
-          float4 pp = __ldg((const float4*)(pin + o));
-          v = rr * f4(1.0f / hq[tid + BT * s]) + bet * pp;
-        }
-        tile[htile[s]] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (idx[s] < 0) continue;
-        int l = tid + BT * s;
-        int c = (l & 7) + 1 + 10 * (((l >> 3) & 7) + 1) + 100 * ((l >> 6) + 1);
-        const size_t o = (size_t)idx[s] * R + 4 * ch;
-        float4 ns = ((tile[c - 1] + tile[c + 1]) + (tile[c - 10] + tile[c + 10])) + (tile[c - 100] + tile[c + 100]);
-        float4 y = f4(qv[s]) * tile[c] - f4(lam) * ns;
-        *(float4*)(yout + o) = y;
-        *(float4*)(pout + o) = val[s];
-        acc[ch][0] += (double)val[s].x * y.x;
-        acc[ch][1] += (double)val[s].y * y.y;
-        acc[ch][2] += (double)val[s].z * y.z;
-        acc[ch][3] += (double)val[s].w * y.w;
-      }
-      __syncthreads();
-    }
-  }
-  const int nblk = gridDim.x;
-#pragma unroll
-  for (int ch = 0; ch < NCH; ++ch) {
-    double v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      v[k] = acc[ch][k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    }
-    if ((tid & 31) == 0) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) red[tid >> 5][k] = v[k];
-    }
-    __syncthreads();
-    if (tid < 4) part[(size_t)(4 * ch + tid) * nblk + blockIdx.x] = red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
-    __syncthreads();
-  }
-  if (!arrive_last(&st->cntA)) return;
-  __shared__ double tot[3][MAXR];
-  sum_partials<1>(part, R, nblk, tot);
-  if (tid < R) {
-    int c = tid;
-    double pq = tot[0][c];
-    st->pq[c] = pq;
-    if (st->done[c]) {
-      st->alpha[c] = 0.0;
-    } else if (!(pq > 0.0) || !isfinite(pq)) {
-      st->alpha[c] = 0.0;
-      st->done[c] = 1;
-      st->status = 2;
-    } else {
-      st->alpha[c] = st->rho[c] / pq;
-    }
+    for (int k = 0; k < NV; ++k) sh[w][k][lane] = v[k];
   }
   __syncthreads();
-  if (tid == 0) st->cntA = 0;
+  if (threadIdx.x < NV * R) {
+    const int k = threadIdx.x / R, c = threadIdx.x % R;
+    double s = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q][k][c];
+    part[((size_t)k * R + c) * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+  }
 }
 
-struct D4 {
-  double v[4];
-};
+// rows [row0, row1) of this CTA: contiguous slices, so a brick and most of its
+// face neighbours are handled by the same CTA (L1 reuse of neighbour rows)
+__device__ __forceinline__ void cta_rows(int N, int* row0, int* row1) {
+  int per = (N + gridDim.x - 1) / gridDim.x;
+  *row0 = min(N, (int)blockIdx.x * per);
+  *row1 = min(N, *row0 + per);
+}
 
-// True residual of the FP64 master iterate, per column: r = z - Q x64
-// (FP64), stored as the FP32 right-hand side of the next correction solve;
-// p = 0; per-column r.r, r.(r/qd), z.z.  The last CTA sets up the inner
-// solve: rhs norm, rho, per-column relative target eta, stop flags.
+__device__ __forceinline__ void load_nb6(const int32_t* __restrict__ nb6, int row, int nb[6]) {
+  const int2 n01 = __ldg((const int2*)(nb6 + 6 * (size_t)row));
+  const int2 n23 = __ldg((const int2*)(nb6 + 6 * (size_t)row + 2));
+  const int2 n45 = __ldg((const int2*)(nb6 + 6 * (size_t)row + 4));
+  nb[0] = n01.x; nb[1] = n01.y; nb[2] = n23.x; nb[3] = n23.y; nb[4] = n45.x; nb[5] = n45.y;
+}
+
+// True residual of the FP64 master iterates, per column: r = z - Q x64 with
+// FP64 arithmetic, stored as the FP32 right-hand side (r[0]) of the next
+// correction solve; per-column r.r and z.z.  The last CTA sets, per column,
+// the stop flag (true residual within tolerance) and the correction target
+// eta = 0.5 tol |z| / |r| clamped to [1e-5, 0.5].
 template <int R>
-__global__ void __launch_bounds__(BT) k_blk_outer(BandView B, float lam, const float* __restrict__ qd,
-                                                  const double* __restrict__ x64, float* __restrict__ rout,
-                                                  float* __restrict__ pout, const __nv_bfloat16* __restrict__ Z,
-                                                  double* part, BlkState* st) {
-  constexpr int NCH = R / 4;
-  __shared__ D4 tile[1000];
-  __shared__ MetaWord sm[7][16];
-  __shared__ double red[4][12];
-  const int tid = threadIdx.x;
-  double acc[3][NCH][4];
+__global__ void __launch_bounds__(CT) k_blk_outer(const BlkArgs* __restrict__ A, BlkState* st) {
+  const int N = A->N;
+  const float lam = A->lam;
+  const int lane = threadIdx.x & 31, c = lane % R;
+  constexpr int RPW = 32 / R;
+  const int wrp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* __restrict__ x64 = A->x64;
+  int row0, row1;
+  cta_rows(N, &row0, &row1);
+  double acc[2] = {0.0, 0.0};
+  for (int row = row0 + wrp * RPW + lane / R; row < row1; row += nw * RPW) {
+    const size_t o = (size_t)row * R + c;
+    int nb[6];
+    load_nb6(A->nb6, row, nb);
+    double ns = 0.0;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int ch = 0; ch < NCH; ++ch)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) acc[a][ch][k] = 0.0;
-  for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
-    __syncthreads();
-    if (tid < 7 * 16) {
-      int which = tid >> 4, w = tid & 15;
-      int r = which == 0 ? b : __ldg(B.nbr + 6 * b + which - 1);
-      MetaWord m;
-      m.bits = 0;
-      m.base = 0;
-      if (r >= 0) m = B.meta[16 * r + w];
-      sm[which][w] = m;
-    }
-    __syncthreads();
-    int idx[4], hidx[3], htile[3];
-    float qv[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      int l = tid + BT * s;
-      MetaWord m = sm[0][l >> 5];
-      uint32_t bit = 1u << (l & 31);
-      idx[s] = (m.bits & bit) ? m.base + __popc(m.bits & (bit - 1u)) : -1;
-      qv[s] = idx[s] >= 0 ? __ldg(qd + idx[s]) : 1.0f;
-    }
-#pragma unroll
-    for (int s = 0; s < 3; ++s) halo_slot(sm, tid + BT * s, &hidx[s], &htile[s]);
-    for (int ch = 0; ch < NCH; ++ch) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        D4 v = {{0.0, 0.0, 0.0, 0.0}};
-        if (idx[s] >= 0) {
-          const double* src = x64 + (size_t)idx[s] * R + 4 * ch;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) v.v[k] = src[k];
-        }
-        int l = tid + BT * s;
-        tile[(l & 7) + 1 + 10 * (((l >> 3) & 7) + 1) + 100 * ((l >> 6) + 1)] = v;
-      }
-#pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        D4 v = {{0.0, 0.0, 0.0, 0.0}};
-        if (hidx[s] >= 0) {
-          const double* src = x64 + (size_t)hidx[s] * R + 4 * ch;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) v.v[k] = src[k];
-        }
-        tile[htile[s]] = v;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (idx[s] < 0) continue;
-        int l = tid + BT * s;
-        int c = (l & 7) + 1 + 10 * (((l >> 3) & 7) + 1) + 100 * ((l >> 6) + 1);
-        const size_t o = (size_t)idx[s] * R + 4 * ch;
-        float rc[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          double ns = ((tile[c - 1].v[k] + tile[c + 1].v[k]) + (tile[c - 10].v[k] + tile[c + 10].v[k])) +
-                      (tile[c - 100].v[k] + tile[c + 100].v[k]);
-          double zb = (double)__bfloat162float(Z[o + k]);
-          double r = zb - ((double)qv[s] * tile[c].v[k] - (double)lam * ns);
-          rc[k] = (float)r;
-          acc[0][ch][k] += r * r;
-          acc[1][ch][k] += r * r / (double)qv[s];
-          acc[2][ch][k] += zb * zb;
-        }
-        *(float4*)(rout + o) = make_float4(rc[0], rc[1], rc[2], rc[3]);
-        *(float4*)(pout + o) = f4(0.0f);
-      }
-      __syncthreads();
-    }
+    for (int k = 0; k < 6; ++k)
+      if (nb[k] >= 0) ns += x64[(size_t)nb[k] * R + c];
+    const double z = (double)__bfloat162float(A->Z[o]);
+    const double r = z - ((double)__ldg(A->qd + row) * x64[o] - (double)lam * ns);
+    A->r[0][o] = (float)r;
+    acc[0] += r * r;
+    acc[1] += z * z;
   }
-  const int nblk = gridDim.x;
-  for (int ch = 0; ch < NCH; ++ch) {
-    double v[12];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        double x = acc[a][ch][k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        v[4 * a + k] = x;
-      }
-    if ((tid & 31) == 0) {
-#pragma unroll
-      for (int q = 0; q < 12; ++q) red[tid >> 5][q] = v[q];
-    }
-    __syncthreads();
-    if (tid < 12) {
-      int a = tid >> 2, k = tid & 3;
-      part[((size_t)a * R + 4 * ch + k) * nblk + blockIdx.x] = red[0][tid] + red[1][tid] + red[2][tid] + red[3][tid];
-    }
-    __syncthreads();
-  }
-  if (!arrive_last(&st->cntR)) return;
+  column_partials<R, 2>(acc, A->part);
+  if (!arrive_last(&st->cnt)) return;
   __shared__ double tot[3][MAXR];
-  sum_partials<3>(part, R, nblk, tot);
-  if (tid < R) {
-    int c = tid;
-    const double rr = tot[0][c], bb = tot[2][c];
-    st->rr0[c] = rr;
-    st->bb0[c] = bb;
-    st->rr[c] = rr;
-    st->bb[c] = rr;
-    st->rho[c] = tot[1][c];
-    st->beta[c] = 0.0;
-    st->alpha[c] = 0.0;
-    const int conv = (c >= st->ncols) || rr <= st->tol0 * st->tol0 * bb || bb == 0.0;
+  sum_partials<2>(A->part, R, gridDim.x, tot);
+  if (threadIdx.x < R) {
+    const int cc = threadIdx.x;
+    const double rr = tot[0][cc], bb = tot[1][cc];
+    st->rr0[cc] = rr;
+    st->bb0[cc] = bb;
+    st->bb[cc] = rr;  // the correction solve's right-hand side norm
+    const int conv = (cc >= st->ncols) || rr <= st->tol0 * st->tol0 * bb || bb == 0.0;
     double eta = conv ? 0.5 : 0.5 * st->tol0 * sqrt(bb / rr);
-    eta = fmin(fmax(eta, 1e-5), 0.5);
-    st->tol2[c] = eta * eta;
-    st->done[c] = conv;
+    eta = fmin(fmax(eta, ETA_MIN), 0.5);
+    st->tol2[cc] = eta * eta;
+    st->done[cc] = conv;
   }
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     int all = 1;
-    for (int c = 0; c < R; ++c) all &= st->done[c];
+    for (int q = 0; q < R; ++q) all &= st->done[q];
     if (all && st->status != 2) st->status = 0;
     if (!all && st->iter >= st->max_iter) st->status = 1;
     st->all_done = all || st->iter >= st->max_iter || st->status == 2;
-    st->cntR = 0;
+    st->first = 1;
+    st->cnt = 0;
     st->guard = 0;
   }
 }
 
-template <int R>
-__global__ void __launch_bounds__(UT) k_blk_update(int N, const float* __restrict__ qd, float* __restrict__ x,
-                                                   const float* __restrict__ p, const float* __restrict__ q,
-                                                   float* __restrict__ r, double* part, BlkState* st,
-                                                   cudaGraphConditionalHandle handle) {
+// Pass 1 of an iteration (streaming, float4 over 4 columns of a row, in
+// place): with u = r/qd,
+//   INIT:   u;                     x = p = s = 0
+//   normal: p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
+//           u = r/qd
+// and the per-column partial sums gamma = r.u, r.r -> part[0..1].
+template <int R, bool INIT>
+__global__ void __launch_bounds__(CT) k_blk_upd(const BlkArgs* __restrict__ A, const BlkState* __restrict__ st) {
+  if (!INIT && st->all_done) return;
   constexpr int G = R / 4;
-  if (st->all_done) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(handle, 0);
-    return;
+  const int N = A->N;
+  const int g = threadIdx.x % G;  // column group of this thread (fixed: the stride is a multiple of G)
+  float4 al = make_float4(0.f, 0.f, 0.f, 0.f), be = al;
+  if (!INIT) {
+    al = make_float4((float)st->alpha[4 * g], (float)st->alpha[4 * g + 1], (float)st->alpha[4 * g + 2],
+                     (float)st->alpha[4 * g + 3]);
+    be = make_float4((float)st->beta[4 * g], (float)st->beta[4 * g + 1], (float)st->beta[4 * g + 2],
+                     (float)st->beta[4 * g + 3]);
   }
-  const int g = threadIdx.x % G;
-  const float4 al = make_float4((float)st->alpha[4 * g], (float)st->alpha[4 * g + 1], (float)st->alpha[4 * g + 2],
-                                (float)st->alpha[4 * g + 3]);
-  double rz[4] = {0, 0, 0, 0}, rr[4] = {0, 0, 0, 0};
+  float4* __restrict__ r = (float4*)A->r[0];
+  float4* __restrict__ w = (float4*)A->w[0];
+  float4* __restrict__ sv = (float4*)A->s[0];
+  float4* __restrict__ p = (float4*)A->p;
+  float4* __restrict__ x = (float4*)A->x;
+  float4* __restrict__ u = (float4*)A->u;
+  const float* __restrict__ iq = A->iq;
+  double acc[8];
+  float fa[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    acc[k] = 0.0;
+    fa[k] = 0.0f;
+  }
+  int nchunk = 0;
   const int64_t n4 = (int64_t)N * G;
-  for (int64_t e = (int64_t)blockIdx.x * UT + threadIdx.x; e < n4; e += (int64_t)gridDim.x * UT) {
-    int64_t i = e / G;
-    float4 pi = ((const float4*)p)[e], qi = ((const float4*)q)[e];
-    float4 xi = ((float4*)x)[e], ri = ((float4*)r)[e];
-    xi = xi + al * pi;
-    ri = ri - al * qi;
-    ((float4*)x)[e] = xi;
-    ((float4*)r)[e] = ri;
-    double iq = 1.0 / (double)__ldg(qd + i);
-    double a0 = ri.x, a1 = ri.y, a2 = ri.z, a3 = ri.w;
-    rr[0] += a0 * a0; rr[1] += a1 * a1; rr[2] += a2 * a2; rr[3] += a3 * a3;
-    rz[0] += a0 * a0 * iq; rz[1] += a1 * a1 * iq; rz[2] += a2 * a2 * iq; rz[3] += a3 * a3 * iq;
-  }
-  __shared__ double gs[8][8];
-  double v[8] = {rz[0], rz[1], rz[2], rz[3], rr[0], rr[1], rr[2], rr[3]};
-  group_sum<8, UT / 32>(v, G, gs);
-  const int nblk = gridDim.x;
-  if (threadIdx.x < G) {
-    for (int k = 0; k < 4; ++k) {
-      part[((size_t)0 * R + 4 * threadIdx.x + k) * nblk + blockIdx.x] = gs[threadIdx.x][k];
-      part[((size_t)1 * R + 4 * threadIdx.x + k) * nblk + blockIdx.x] = gs[threadIdx.x][4 + k];
+  for (int64_t e = (int64_t)blockIdx.x * CT + threadIdx.x; e < n4; e += (int64_t)gridDim.x * CT) {
+    const float q = iq[e / G];
+    float4 ri = r[e], un;
+    if (INIT) {
+      un = make_float4(ri.x * q, ri.y * q, ri.z * q, ri.w * q);
+      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+      x[e] = z;
+      p[e] = z;
+      sv[e] = z;
+    } else {
+      const float4 wi = w[e], si = sv[e], pi = p[e], xi = x[e];
+      // beta = 0 starts a new direction: do not touch the previous p, s
+      float4 pn, sn;
+      pn.x = ri.x * q + (be.x != 0.f ? be.x * pi.x : 0.f);
+      pn.y = ri.y * q + (be.y != 0.f ? be.y * pi.y : 0.f);
+      pn.z = ri.z * q + (be.z != 0.f ? be.z * pi.z : 0.f);
+      pn.w = ri.w * q + (be.w != 0.f ? be.w * pi.w : 0.f);
+      sn.x = wi.x + (be.x != 0.f ? be.x * si.x : 0.f);
+      sn.y = wi.y + (be.y != 0.f ? be.y * si.y : 0.f);
+      sn.z = wi.z + (be.z != 0.f ? be.z * si.z : 0.f);
+      sn.w = wi.w + (be.w != 0.f ? be.w * si.w : 0.f);
+      x[e] = make_float4(xi.x + al.x * pn.x, xi.y + al.y * pn.y, xi.z + al.z * pn.z, xi.w + al.w * pn.w);
+      ri = make_float4(ri.x - al.x * sn.x, ri.y - al.y * sn.y, ri.z - al.z * sn.z, ri.w - al.w * sn.w);
+      un = make_float4(ri.x * q, ri.y * q, ri.z * q, ri.w * q);
+      p[e] = pn;
+      sv[e] = sn;
+      r[e] = ri;
     }
-  }
-  if (!arrive_last(&st->cntB)) return;
-  __shared__ double tot[3][MAXR];
-  sum_partials<2>(part, R, nblk, tot);
-  __shared__ int any_live;
-  if (threadIdx.x == 0) {
-    any_live = 0;
-    st->iter += 1;
-  }
-  __syncthreads();
-  if (threadIdx.x < R) {
-    int c = threadIdx.x;
-    if (!st->done[c]) {
-      double rho_new = tot[0][c];
-      st->rr[c] = tot[1][c];
-      st->iters[c] += 1;
-      if (!isfinite(rho_new) || !isfinite(tot[1][c])) {
-        st->done[c] = 1;
-        st->status = 2;
-      } else if (tot[1][c] <= st->tol2[c] * st->bb[c]) {
-        st->done[c] = 1;
-      } else {
-        st->beta[c] = rho_new / st->rho[c];
-        st->rho[c] = rho_new;
-        atomicOr(&any_live, 1);
+    u[e] = un;
+    fa[0] += ri.x * un.x; fa[1] += ri.y * un.y; fa[2] += ri.z * un.z; fa[3] += ri.w * un.w;
+    fa[4] += ri.x * ri.x; fa[5] += ri.y * ri.y; fa[6] += ri.z * ri.z; fa[7] += ri.w * ri.w;
+    if (++nchunk == 8) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        acc[k] += (double)fa[k];
+        fa[k] = 0.0f;
       }
+      nchunk = 0;
     }
-    if (st->done[c]) st->beta[c] = 0.0;
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k] += (double)fa[k];
+  // per-column CTA sums: lanes sharing threadIdx % G, then warps
+  __shared__ double sh[CT / 32][8][8];
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    for (int o = 16; o >= G; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+  if (lane < G) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[wrp][lane][k] = acc[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    if (!any_live || st->iter >= st->max_iter) {
-      st->all_done = 1;
-      cudaGraphSetConditional(handle, 0);
-    }
-    st->cntB = 0;
+  if (threadIdx.x < 2 * R) {
+    const int q = threadIdx.x / R, c = threadIdx.x % R;  // q: 0 = r.u, 1 = r.r
+    double t = 0.0;
+    for (int ww = 0; ww < CT / 32; ++ww) t += sh[ww][c / 4][4 * q + (c & 3)];
+    A->part1[((size_t)q * R + c) * gridDim.x + blockIdx.x] = t;
   }
 }
 
-// Z[i][c] = Rademacher(seed, k0 + c, lin_i) for c < ncols, 0 beyond; x = 0
+// Pass 2: w = Q u (7-point, u gathered from the six neighbour rows), the
+// per-column partial w.u, and -- in the last CTA -- the scalar update
+// (first pass of a correction solve: alpha = gamma/delta, beta = 0;
+// afterwards the single-reduction recurrence and the stop test on r.r).
+// Each warp takes 32 consecutive rows at a time: lane l loads the neighbour
+// indices and Q_jj of row l once, then they are broadcast by shuffles.
+template <int R>
+__global__ void __launch_bounds__(CT) k_blk_spmm(const BlkArgs* __restrict__ A, BlkState* st,
+                                                 cudaGraphConditionalHandle handle, int bench) {
+  if (!bench && blockIdx.x == 0 && threadIdx.x == 0) {
+    st->nexec += 2;  // this kernel and the update pass before it
+    unsigned gd = atomicAdd(&st->guard, 1u);
+    if (st->all_done || gd > 2u * (unsigned)st->max_iter + 64u) {
+      if (!st->all_done) {
+        st->status = 1;
+        st->all_done = 1;
+      }
+      cudaGraphSetConditional(handle, 0);
+    }
+  }
+  if (!bench && st->all_done) return;
+  const int N = A->N;
+  const float lam = A->lam;
+  const int lane = threadIdx.x & 31, c = lane % R;
+  constexpr int RPW = 32 / R;
+  const int wrp = threadIdx.x >> 5, nw = CT / 32;
+  const float* __restrict__ u = A->u;
+  float* __restrict__ w = A->w[0];
+  double acc = 0.0;
+  float fa = 0.0f;
+  int nchunk = 0;
+  int row0, row1;
+  cta_rows(N, &row0, &row1);
+  for (int base = row0 + 32 * wrp; base < row1; base += 32 * nw) {
+    int nbl[6] = {-1, -1, -1, -1, -1, -1};
+    float ql = 0.0f;
+    if (base + lane < row1) {
+      load_nb6(A->nb6, base + lane, nbl);
+      ql = __ldg(A->qd + base + lane);
+    }
+#pragma unroll 2
+    for (int j = 0; j < 32 / RPW; ++j) {
+      const int src = j * RPW + lane / R;
+      const int row = base + src;
+      int nb[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) nb[k] = __shfl_sync(0xffffffffu, nbl[k], src);
+      const float q = __shfl_sync(0xffffffffu, ql, src);
+      if (row >= row1) continue;
+      const size_t o = (size_t)row * R + c;
+      const float uo = u[o];
+      float un[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) un[k] = nb[k] >= 0 ? u[(size_t)nb[k] * R + c] : 0.0f;
+      const float ns = ((un[0] + un[1]) + (un[2] + un[3])) + (un[4] + un[5]);
+      const float wn = q * uo - lam * ns;
+      w[o] = wn;
+      fa += wn * uo;
+      if (++nchunk == 8) {
+        acc += (double)fa;
+        fa = 0.0f;
+        nchunk = 0;
+      }
+    }
+  }
+  acc += (double)fa;
+  double v[1] = {acc};
+  column_partials<R, 1>(v, A->part);
+  if (!arrive_last(&st->cnt)) return;
+  if (bench) {  // timing only: scalars stay as they are
+    if (threadIdx.x == 0) st->cnt = 0;
+    return;
+  }
+  __shared__ double tot[3][MAXR];
+  __shared__ double tot1[3][MAXR];
+  __shared__ int any_live;
+  sum_partials<1>(A->part, R, gridDim.x, tot);
+  sum_partials<2>(A->part1, R, gridDim.x, tot1);  // pass 1: r.u, r.r
+  const bool first = st->first;
+  if (threadIdx.x == 0) {
+    any_live = 0;
+    if (!first) st->iter += 1;
+  }
+  __syncthreads();
+  if (threadIdx.x < R) {
+    const int cc = threadIdx.x;
+    const double g = tot1[0][cc], rr = tot1[1][cc], d = tot[0][cc];
+    if (!st->done[cc]) {
+      if (first) {
+        st->gamma[cc] = g;
+        st->beta[cc] = 0.0;
+        if (!(d > 0.0) || !isfinite(d) || !isfinite(g)) {
+          st->done[cc] = 1;
+          st->status = 2;
+        } else {
+          st->alpha[cc] = g / d;
+          atomicOr(&any_live, 1);
+        }
+      } else {
+        st->rr[cc] = rr;
+        st->iters[cc] += 1;
+        if (!isfinite(g) || !isfinite(d) || !isfinite(rr)) {
+          st->done[cc] = 1;
+          st->status = 2;
+        } else if (rr <= st->tol2[cc] * st->bb[cc]) {
+          st->done[cc] = 1;
+        } else {
+          const double beta = g / st->gamma[cc];
+          const double den = d - beta * g / st->alpha[cc];
+          if (!(den > 0.0) || !isfinite(den)) {
+            st->done[cc] = 1;
+            st->status = 2;
+          } else {
+            st->beta[cc] = beta;
+            st->alpha[cc] = g / den;
+            st->gamma[cc] = g;
+            atomicOr(&any_live, 1);
+          }
+        }
+      }
+    }
+    if (st->done[cc]) {
+      st->alpha[cc] = 0.0;
+      st->beta[cc] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->first = 0;
+    if (!any_live || st->iter >= st->max_iter) {
+      st->all_done = 1;
+      if (!first) cudaGraphSetConditional(handle, 0);
+    }
+    st->cnt = 0;
+  }
+}
+
+// Z[i][c] = Rademacher(seed, k0 + c, lin_i) for c < ncols, 0 beyond; x64 = 0
+// and the first correction right-hand side r = z - Q 0 = z
 template <int R>
 __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed, int k0, int ncols,
-                         __nv_bfloat16* __restrict__ Z, double* __restrict__ x) {
+                         __nv_bfloat16* __restrict__ Z, double* __restrict__ x, float* __restrict__ r0) {
   const int64_t n = (int64_t)N * R;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / R;
@@ -507,10 +458,11 @@ __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed,
     }
     Z[e] = __float2bfloat16(z);
     x[e] = 0.0;
+    r0[e] = z;
   }
 }
 
-// s_acc[i] += sum_c z[i][c] x[i][c]
+// s_acc[i] += sum_c z[i][c] x64[i][c]
 template <int R>
 __global__ void k_hutch(int N, const __nv_bfloat16* __restrict__ Z, const double* __restrict__ x,
                         double* __restrict__ sacc) {
@@ -531,13 +483,38 @@ __global__ void k_axpy64(int64_t n, const float* __restrict__ d, double* __restr
     x[i] += (double)d[i];
 }
 
-__global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols) {
+// per-voxel indices of the six face neighbours (-x, +x, -y, +y, -z, +z), -1 outside the band
+__global__ void k_nb6(BandView B, int32_t* __restrict__ nb6) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < B.N; v += gridDim.x * blockDim.x) {
+    int L = B.lin[v];
+    int i = L % B.n, j = (L / B.n) % B.n, k = L / (B.n * B.n);
+    nb6[6 * (size_t)v + 0] = band_lookup(B, i - 1, j, k);
+    nb6[6 * (size_t)v + 1] = band_lookup(B, i + 1, j, k);
+    nb6[6 * (size_t)v + 2] = band_lookup(B, i, j - 1, k);
+    nb6[6 * (size_t)v + 3] = band_lookup(B, i, j + 1, k);
+    nb6[6 * (size_t)v + 4] = band_lookup(B, i, j, k - 1);
+    nb6[6 * (size_t)v + 5] = band_lookup(B, i, j, k + 1);
+  }
+}
+
+__global__ void k_inv(int N, const float* __restrict__ qd, float* __restrict__ iq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) iq[i] = 1.0f / qd[i];
+}
+
+// State for a new block of probes.  With x64 = 0 the true residual is z
+// itself, so |r|^2 = |z|^2 = N for every live column and no FP64 pass is
+// needed before the first correction solve.
+__global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, int N, double eta_min) {
   int c = threadIdx.x;
   if (c < MAXR) {
-    st->done[c] = 0;
+    const int live = c < ncols;
+    st->done[c] = !live;
     st->iters[c] = 0;
     st->beta[c] = 0.0;
     st->alpha[c] = 0.0;
+    st->rr0[c] = st->bb0[c] = st->bb[c] = live ? (double)N : 0.0;
+    const double eta = fmin(fmax(0.5 * tol, eta_min), 0.5);
+    st->tol2[c] = eta * eta;
   }
   if (c == 0) {
     st->tol0 = tol;
@@ -546,9 +523,22 @@ __global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols) {
     st->all_done = 0;
     st->status = 0;
     st->ncols = ncols;
-    st->cntA = st->cntB = st->cntR = 0;
+    st->first = 1;
+    st->cnt = 0;
     st->guard = 0;
     st->nexec = 0;
+  }
+}
+
+__global__ void k_bench_state(BlkState* st) {
+  int c = threadIdx.x;
+  if (c < MAXR) {
+    st->beta[c] = 0.0;  // bounded values over repeated launches
+    st->alpha[c] = 0.0;
+  }
+  if (c == 0) {
+    st->cnt = 0;
+    st->all_done = 0;
   }
 }
 
@@ -562,107 +552,129 @@ unsigned grid_for(int64_t n, int threads, int64_t cap) {
 
 struct BlockGraph {
   int R = 0;
-  int64_t N = 0;
-  float *x = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;  // FP32 correction solve
-  double* x64 = nullptr;                                                        // FP64 master iterates
+  int64_t cap_rows = 0;
+  BlkArgs h;                    // host copy of the argument block
+  BlkArgs* h_pin = nullptr;     // pinned staging for the upload
+  BlkArgs* d_args = nullptr;
   __nv_bfloat16* Z = nullptr;
   double* sacc = nullptr;
-  double* part = nullptr;
   BlkState* st = nullptr;
   BlkState* h_st = nullptr;
-  int nblkA = 0, nblkB = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
 };
+
+static void free_arrays(BlockGraph* g) {
+  void* ptrs[] = {g->h.r[0], g->h.w[0], g->h.s[0], g->h.p, g->h.x, g->h.u, g->h.x64,
+                  g->h.iq, g->h.part, g->h.part1, g->Z, g->sacc};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  g->cap_rows = 0;
+}
 
 void block_graph_free(BlockGraph* g) {
   if (!g) return;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   if (g->cap) cudaStreamDestroy(g->cap);
-  cudaFree(g->x);
-  cudaFree(g->x64);
-  cudaFree(g->r);
-  cudaFree(g->p0);
-  cudaFree(g->p1);
-  cudaFree(g->q);
-  cudaFree(g->Z);
-  cudaFree(g->sacc);
-  cudaFree(g->part);
-  cudaFree(g->st);
+  free_arrays(g);
+  if (g->d_args) cudaFree(g->d_args);
+  if (g->st) cudaFree(g->st);
   if (g->h_st) cudaFreeHost(g->h_st);
+  if (g->h_pin) cudaFreeHost(g->h_pin);
   delete g;
 }
 
 template <int R>
-static void blk_A(const BandView& bv, const bf_band* b, BlockGraph* g, const float* pin, float* pout, cudaStream_t s,
-                  cudaGraphConditionalHandle h) {
-  k_blk_spmv<R><<<g->nblkA, BT, 0, s>>>(bv, (float)b->prm.lambda, b->qd, pin, g->r, pout, g->q, g->part, g->st, h);
+static void blk_iter(BlockGraph* g, cudaStream_t s, cudaGraphConditionalHandle h, int bench = 0) {
+  k_blk_upd<R, false><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
+  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, h, bench);
+}
+
+// start of a correction solve from r: u, p = s = x = 0, w = Q u, alpha
+template <int R>
+static void blk_start(BlockGraph* g, cudaStream_t s) {
+  k_blk_upd<R, true><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
+  count_launch();
+  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), 0);
+  count_launch();
 }
 
 template <int R>
-static void blk_B(const bf_band* b, BlockGraph* g, const float* p, cudaStream_t s, cudaGraphConditionalHandle h) {
-  k_blk_update<R><<<g->nblkB, UT, 0, s>>>((int)b->N, b->qd, g->x, p, g->q, g->r, g->part, g->st, h);
+static void blk_outer(BlockGraph* g, cudaStream_t s) {
+  k_blk_outer<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
+  count_launch();
+  blk_start<R>(g, s);
 }
 
-template <int R>
-static void blk_outer(const BandView& bv, const bf_band* b, BlockGraph* g, cudaStream_t s) {
-  k_blk_outer<R><<<g->nblkA, BT, 0, s>>>(bv, (float)b->prm.lambda, b->qd, g->x64, g->r, g->p0, g->Z, g->part, g->st); count_launch();
-}
+static int ridx(int R) { return R == 8 ? 0 : (R == 16 ? 1 : 2); }
 
+// The context's block solver for width R, with workspaces for >= N rows and
+// the argument block pointing at band b.
 template <int R>
-static bf_status get_block_graph(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
-  BlockGraph* g = b->bg;
-  if (g && (g->R != R || g->N != b->N)) {
-    cudaStreamSynchronize(ctx->stream);
-    block_graph_free(g);
-    g = b->bg = nullptr;
-  }
+static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
+  BlockGraph*& g = ctx->blk[ridx(R)];
+  cudaStream_t s = ctx->stream;
   if (!g) {
     g = new BlockGraph();
-    b->bg = g;
     g->R = R;
-    g->N = b->N;
-    size_t nv = (size_t)(b->N ? b->N : 1) * R;
-    BF_CK(cudaMalloc(&g->x, nv * 4));
-    BF_CK(cudaMalloc(&g->x64, nv * 8));
-    BF_CK(cudaMalloc(&g->r, nv * 4));
-    BF_CK(cudaMalloc(&g->p0, nv * 4));
-    BF_CK(cudaMalloc(&g->p1, nv * 4));
-    BF_CK(cudaMalloc(&g->q, nv * 4));
-    BF_CK(cudaMalloc(&g->Z, nv * 2));
-    BF_CK(cudaMalloc(&g->sacc, (size_t)(b->N ? b->N : 1) * 8));
-    g->nblkA = (int)(b->NB < 152 * 8 ? b->NB : 152 * 8);
-    if (g->nblkA < 1) g->nblkA = 1;
-    g->nblkB = (int)grid_for((int64_t)b->N * (R / 4), UT * 4, 152 * 8);
-    int np = g->nblkA > g->nblkB ? g->nblkA : g->nblkB;
-    BF_CK(cudaMalloc(&g->part, (size_t)3 * R * np * sizeof(double)));
+    memset(&g->h, 0, sizeof(g->h));
+    BF_CK(cudaMalloc(&g->d_args, sizeof(BlkArgs)));
+    BF_CK(cudaMallocHost(&g->h_pin, sizeof(BlkArgs)));
     BF_CK(cudaMalloc(&g->st, sizeof(BlkState)));
     BF_CK(cudaMallocHost(&g->h_st, sizeof(BlkState)));
-    BandView bv = band_view(b);
     BF_CK(cudaGraphCreate(&g->graph, 0));
     cudaGraphConditionalHandle h;
     BF_CK(cudaGraphConditionalHandleCreate(&h, g->graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams np2 = {};
-    np2.type = cudaGraphNodeTypeConditional;
-    np2.conditional.handle = h;
-    np2.conditional.type = cudaGraphCondTypeWhile;
-    np2.conditional.size = 1;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
     cudaGraphNode_t node;
-    BF_CK(cudaGraphAddNode(&node, g->graph, nullptr, nullptr, 0, &np2));
-    cudaGraph_t body = np2.conditional.phGraph_out[0];
+    BF_CK(cudaGraphAddNode(&node, g->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
     BF_CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
     BF_CK(cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    blk_A<R>(bv, b, g, g->p0, g->p1, g->cap, h);
-    blk_B<R>(b, g, g->p1, g->cap, h);
-    blk_A<R>(bv, b, g, g->p1, g->p0, g->cap, h);
-    blk_B<R>(b, g, g->p0, g->cap, h);
+    blk_iter<R>(g, g->cap, h);
     cudaGraph_t ob;
     cudaError_t e = cudaStreamEndCapture(g->cap, &ob);
     if (e != cudaSuccess) return bf_fail(ctx, BF_ECUDA, "capture block PCG body", cudaGetErrorString(e));
     BF_CK(cudaGraphInstantiate(&g->exec, g->graph, 0));
   }
+  if (b->N > g->cap_rows) {
+    BF_CK(cudaStreamSynchronize(s));
+    free_arrays(g);
+    const int64_t rows = b->N + b->N / 8 + 1024;
+    const size_t nv = (size_t)rows * R;
+    BF_CK(cudaMalloc(&g->h.r[0], nv * 4));
+    BF_CK(cudaMalloc(&g->h.w[0], nv * 4));
+    BF_CK(cudaMalloc(&g->h.s[0], nv * 4));
+    BF_CK(cudaMalloc(&g->h.u, nv * 4));
+    BF_CK(cudaMalloc(&g->h.p, nv * 4));
+    BF_CK(cudaMalloc(&g->h.x, nv * 4));
+    BF_CK(cudaMalloc(&g->h.x64, nv * 8));
+    BF_CK(cudaMalloc(&g->Z, nv * 2));
+    BF_CK(cudaMalloc(&g->h.iq, (size_t)rows * 4));
+    BF_CK(cudaMalloc(&g->sacc, (size_t)rows * 8));
+    BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NCTA * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.part1, (size_t)2 * R * NCTA * sizeof(double)));
+    g->cap_rows = rows;
+  }
+  if (!b->nb6) {
+    BF_TRY(dev_alloc_t(ctx, &b->nb6, (size_t)6 * (b->N ? b->N : 1)));
+    k_nb6<<<grid_for(b->N, 256, 152 * 16), 256, 0, s>>>(band_view(b), b->nb6);
+    count_launch();
+  }
+  g->h.N = (int)b->N;
+  g->h.lam = (float)b->prm.lambda;
+  g->h.nb6 = b->nb6;
+  g->h.qd = b->qd;
+  g->h.Z = g->Z;
+  // the previous upload from h_pin has completed: every solve ends with a sync
+  *g->h_pin = g->h;
+  BF_CK(cudaMemcpyAsync(g->d_args, g->h_pin, sizeof(BlkArgs), cudaMemcpyHostToDevice, s));
   *out = g;
   return BF_OK;
 }
@@ -672,10 +684,11 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, doubl
                             int* total_iters) {
   cudaStream_t s = ctx->stream;
   BlockGraph* g = nullptr;
-  BF_TRY(get_block_graph<R>(ctx, b, &g));
-  BandView bv = band_view(b);
+  BF_TRY(get_block_solver<R>(ctx, b, &g));
   const int N = (int)b->N;
   BF_CK(cudaMemsetAsync(g->sacc, 0, (size_t)N * 8, s));
+  k_inv<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, b->qd, g->h.iq);
+  count_launch();
   uint64_t mseed = 0;
   {  // host copy of the probe seed mix (same function as the device)
     uint64_t z = seed + 0x9E3779B97F4A7C15ULL;
@@ -690,9 +703,11 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, doubl
   for (int k0 = 0; k0 < K; k0 += R) {
     // one block of R probes: FP64 master iterates, FP32 correction solves
     int ncols = K - k0 < R ? K - k0 : R;
-    k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->x64); count_launch();
-    k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols); count_launch();
-    blk_outer<R>(bv, b, g, s);
+    k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.x64, g->h.r[0]);
+    count_launch();
+    k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols, N, ETA_MIN);
+    count_launch();
+    blk_start<R>(g, s);
     BF_CK(cudaGetLastError());
     bool done = false;
     for (int outer = 0; outer < 64; ++outer) {
@@ -702,58 +717,54 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, doubl
         done = true;
         break;
       }
-      BF_CK(cudaMemsetAsync(g->x, 0, (size_t)NR * 4, s));
       BF_CK(cudaGraphLaunch(g->exec, s));
-      k_axpy64<<<gNR, 256, 0, s>>>(NR, g->x, g->x64); count_launch();
-      blk_outer<R>(bv, b, g, s);
+      k_axpy64<<<gNR, 256, 0, s>>>(NR, g->h.x, g->h.x64);
+      count_launch();
+      blk_outer<R>(g, s);
       BF_CK(cudaGetLastError());
     }
     const BlkState& h = *g->h_st;
     count_launch(h.nexec);
     for (int c = 0; c < ncols; ++c) tot_it += h.iters[c];
-    k_hutch<R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->Z, g->x64, g->sacc); count_launch();
+    k_hutch<R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->Z, g->h.x64, g->sacc);
+    count_launch();
     BF_CK(cudaGetLastError());
     if (h.status == 2) { result = BF_BREAKDOWN; break; }
     if (!done || h.status == 1) { result = BF_NOT_CONVERGED; break; }
   }
-  k_finish<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->sacc, 1.0 / K, s_out); count_launch();
+  k_finish<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->sacc, 1.0 / K, s_out);
+  count_launch();
   BF_CK(cudaGetLastError());
+  BF_CK(cudaStreamSynchronize(s));
   if (total_iters) *total_iters = tot_it;
   if (result == BF_BREAKDOWN) return bf_fail(ctx, BF_BREAKDOWN, "block PCG breakdown");
   if (result == BF_NOT_CONVERGED) return bf_fail(ctx, BF_NOT_CONVERGED, "block PCG iteration limit reached");
   return BF_OK;
 }
 
-namespace {
-__global__ void k_bench_state(BlkState* st) {
-  int c = threadIdx.x;
-  if (c < MAXR) {
-    st->done[c] = 0;
-    st->beta[c] = 0.5;
-    st->rho[c] = 1.0;
-  }
-  if (c == 0) {
-    st->all_done = 0;
-    st->max_iter = 1 << 28;
-    st->guard = 0;
-    st->cntA = 0;
-  }
-}
-
+// which: 0 = one iteration (both passes), 1 = update pass, 2 = SpMM pass
 template <int R>
-bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int reps, double* ms) {
+static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int which, int reps, double* ms) {
   BlockGraph* g = nullptr;
-  BF_TRY(get_block_graph<R>(ctx, b, &g));
+  BF_TRY(get_block_solver<R>(ctx, b, &g));
   cudaStream_t s = ctx->stream;
-  BandView bv = band_view(b);
-  k_bench_state<<<1, MAXR, 0, s>>>(g->st); count_launch();
+  k_inv<<<grid_for(b->N, 256, 152 * 16), 256, 0, s>>>((int)b->N, b->qd, g->h.iq);
+  count_launch();
+  k_bench_state<<<1, MAXR, 0, s>>>(g->st);
+  count_launch();
   cudaEvent_t e0, e1;
   BF_CK(cudaEventCreate(&e0));
   BF_CK(cudaEventCreate(&e1));
   BF_CK(cudaEventRecord(e0, s));
   for (int i = 0; i < reps; ++i) {
-    blk_A<R>(bv, b, g, (i & 1) ? g->p1 : g->p0, (i & 1) ? g->p0 : g->p1, s, cudaGraphConditionalHandle());
-    count_launch();
+    if (which != 2) {
+      k_blk_upd<R, false><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
+      count_launch();
+    }
+    if (which != 1) {
+      k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), 1);
+      count_launch();
+    }
   }
   BF_CK(cudaEventRecord(e1, s));
   BF_CK(cudaEventSynchronize(e1));
@@ -764,13 +775,12 @@ bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int reps, double* ms) {
   *ms = t / reps;
   return BF_OK;
 }
-}  // namespace
 
-bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms) {
+bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms) {
   switch (R) {
-    case 8: return bench_blk_t<8>(ctx, b, reps, ms);
-    case 16: return bench_blk_t<16>(ctx, b, reps, ms);
-    case 32: return bench_blk_t<32>(ctx, b, reps, ms);
+    case 8: return bench_blk_t<8>(ctx, b, which, reps, ms);
+    case 16: return bench_blk_t<16>(ctx, b, which, reps, ms);
+    case 32: return bench_blk_t<32>(ctx, b, which, reps, ms);
   }
   return bf_fail(ctx, BF_EINVAL, "R must be 8, 16 or 32");
 }

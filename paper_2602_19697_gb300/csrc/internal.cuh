@@ -46,6 +46,8 @@ struct bf_ctx {
   size_t mesh_vcap = 0, mesh_tcap = 0;
   int8_t* mc_table = nullptr;   // device [256][16][3] edge triples, -1 padded
   int8_t* mc_ntri = nullptr;    // device [256]
+  BlockGraph* blk[3] = {nullptr, nullptr, nullptr};  // probe solvers, R = 8, 16, 32
+  SolveGraph* sgl[2] = {nullptr, nullptr};           // mean solvers, FP32 and FP64
 };
 
 // Per-brick lookup entry: band bits of 32 local voxels and the compact index
@@ -79,9 +81,7 @@ struct bf_band {
   float* qd = nullptr;        // [N] Q_jj
   float* rhs = nullptr;       // [N] h_j
   bool integrated = false;
-  // solver state (lazily allocated)
-  SolveGraph* sg = nullptr;
-  BlockGraph* bg = nullptr;
+  int32_t* nb6 = nullptr;     // [N][6] face-neighbour indices (probe solver)
 };
 
 // POD view of a band passed to kernels.
@@ -126,7 +126,7 @@ bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, uns
                           double* relres);
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, double tol, int max_iter, int R,
                         unsigned flags, float* s, int* total_iters);
-bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms);
+bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms);
 void solve_graph_free(SolveGraph* g);
 void block_graph_free(BlockGraph* g);
 bf_status mc_impl(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt);

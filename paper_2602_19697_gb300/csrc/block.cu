@@ -311,10 +311,15 @@ __global__ void __launch_bounds__(CT) k_blk_upd(const BlkArgs* __restrict__ A, c
 // afterwards the single-reduction recurrence and the stop test on r.r).
 // Each warp takes 32 consecutive rows at a time: lane l loads the neighbour
 // indices and Q_jj of row l once, then they are broadcast by shuffles.
+// mode: SPMM_GRAPH inside the solver graph (may end the WHILE loop),
+// SPMM_START host-launched start of a correction solve, SPMM_BENCH timing.
+constexpr int SPMM_GRAPH = 0, SPMM_BENCH = 1, SPMM_START = 2;
+
 template <int R>
 __global__ void __launch_bounds__(CT) k_blk_spmm(const BlkArgs* __restrict__ A, BlkState* st,
-                                                 cudaGraphConditionalHandle handle, int bench) {
-  if (!bench && blockIdx.x == 0 && threadIdx.x == 0) {
+                                                 cudaGraphConditionalHandle handle, int mode) {
+  const bool bench = mode == SPMM_BENCH;
+  if (mode == SPMM_GRAPH && blockIdx.x == 0 && threadIdx.x == 0) {
     st->nexec += 2;  // this kernel and the update pass before it
     unsigned gd = atomicAdd(&st->guard, 1u);
     if (st->all_done || gd > 2u * (unsigned)st->max_iter + 64u) {
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(CT) k_blk_spmm(const BlkArgs* __restrict__ A, 
     st->first = 0;
     if (!any_live || st->iter >= st->max_iter) {
       st->all_done = 1;
-      if (!first) cudaGraphSetConditional(handle, 0);
+      if (mode == SPMM_GRAPH) cudaGraphSetConditional(handle, 0);
     }
     st->cnt = 0;
   }
@@ -589,7 +594,7 @@ void block_graph_free(BlockGraph* g) {
 template <int R>
 static void blk_iter(BlockGraph* g, cudaStream_t s, cudaGraphConditionalHandle h, int bench = 0) {
   k_blk_upd<R, false><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
-  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, h, bench);
+  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, h, bench ? SPMM_BENCH : SPMM_GRAPH);
 }
 
 // start of a correction solve from r: u, p = s = x = 0, w = Q u, alpha
@@ -597,7 +602,7 @@ template <int R>
 static void blk_start(BlockGraph* g, cudaStream_t s) {
   k_blk_upd<R, true><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
   count_launch();
-  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), 0);
+  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_START);
   count_launch();
 }
 
@@ -762,7 +767,7 @@ static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int which, int reps, doubl
       count_launch();
     }
     if (which != 1) {
-      k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), 1);
+      k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_BENCH);
       count_launch();
     }
   }

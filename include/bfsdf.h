@@ -191,6 +191,25 @@ bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris);
 bf_status bf_score_views(bf_ctx* ctx, const bf_band* band, const float* mu, const float* s,
                          const float* cand_poses, int V, const bf_intrinsics* K, double eps, double* U, int* best);
 
+/* Allocation-free mean solve, for callers that must not allocate device
+ * memory while they run (a real-time loop with a fixed memory budget, or a
+ * host application that owns the device allocator).  The paper has no
+ * counterpart: it is bf_solve_mean's result (Jacobi PCG, FP32 vectors, FP64
+ * inner products and FP64 true-residual refinement, same stopping rule)
+ * computed with every scratch vector in one fixed array of device memory
+ * that the library declares statically (about 7.4 MB per GPU, present from
+ * library load until process exit).  No graph is used; the host launches
+ * the iterations.
+ *   Limits: band of at most 262,144 voxels (else BF_EINVAL); mu [N] must be
+ *   DEVICE memory (else BF_EINVAL); x0 = 0.  Errors are reported through the
+ *   status only (bf_last_error is not updated).
+ *   The first call on a device looks up the array's device address; make it
+ *   before any stream capture.  All calls share the array: calls whose GPU
+ *   work overlaps (other streams or threads) race and must be serialised by
+ *   the caller. */
+bf_status bf_solve_mean_static(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter, float* mu, int* iters,
+                               double* rel_res);
+
 /* Kernel timing for roofline measurements: launches kernels of the solver
  * `reps` times back to back on the context stream between two CUDA events
  * and returns the mean time per repetition (ms).

@@ -31,7 +31,7 @@ BF_SOLVE_WARM = 2
 EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_build_band", "bf_band_free",
             "bf_band_info", "bf_export_band", "bf_integrate_depth", "bf_reset_observations", "bf_export_system",
             "bf_spmv", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
-            "bf_score_views", "bf_bench_kernel", "bf_launch_count"]
+            "bf_score_views", "bf_solve_mean_static", "bf_bench_kernel", "bf_launch_count"]
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
 BF_KERNEL_BLOCK_UPDATE = 2
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
         "bf_extract_surface": (i, [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "bf_get_surface": (i, [vp, vp, vp]),
         "bf_score_views": (i, [vp, vp, vp, vp, vp, i, ctypes.POINTER(Intrinsics), d, vp, ctypes.POINTER(i)]),
+        "bf_solve_mean_static": (i, [vp, vp, d, i, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "bf_bench_kernel": (i, [vp, vp, i, i, i, ctypes.POINTER(d)]),
         "bf_launch_count": (i, [ctypes.POINTER(i64)]),
     }

@@ -165,6 +165,15 @@ bf_status bf_solve_mean(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter
 bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* band, int K, uint64_t seed, double rel_tol, int max_iter,
                                int rhs_block, unsigned flags, float* s, int* total_iters);
 
+/* Partial probe sum for sharding the estimator across devices or calls
+ * (Sec. 3.7, diag equation): s_sum = sum_{k_begin <= k < k_end} z_k (.)
+ * Q^-1 z_k with the probes of bf_estimate_variance (probe k is a function of
+ * (seed, k, voxel) only), so disjoint ranges summed and divided by K give
+ * bf_estimate_variance's s.  Arguments and errors as bf_estimate_variance. */
+bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* band, int k_begin, int k_end, uint64_t seed,
+                                     double rel_tol, int max_iter, int rhs_block, unsigned flags, float* s_sum,
+                                     int* total_iters);
+
 /* Marching cubes on mu (Sec. 3.8; Algorithm 1 step 7): every cube of 8 band
  * voxels, inside = mu < 0; per cube, polygons traced face by face
  * (ambiguous faces separate the inside corners) and fan-triangulated from

@@ -31,7 +31,8 @@ BF_SOLVE_WARM = 2
 EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_build_band", "bf_band_free",
             "bf_band_info", "bf_export_band", "bf_integrate_depth", "bf_reset_observations", "bf_export_system",
             "bf_spmv", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
-            "bf_score_views", "bf_solve_mean_static", "bf_bench_kernel", "bf_launch_count"]
+            "bf_score_views", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
+            "bf_launch_count"]
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
 BF_KERNEL_BLOCK_UPDATE = 2
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH):
         "bf_get_surface": (i, [vp, vp, vp]),
         "bf_score_views": (i, [vp, vp, vp, vp, vp, i, ctypes.POINTER(Intrinsics), d, vp, ctypes.POINTER(i)]),
         "bf_solve_mean_static": (i, [vp, vp, d, i, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
+        "bf_estimate_variance_range": (i, [vp, vp, i, i, ctypes.c_uint64, d, i, i, u, vp, ctypes.POINTER(i)]),
         "bf_bench_kernel": (i, [vp, vp, i, i, i, ctypes.POINTER(d)]),
         "bf_launch_count": (i, [ctypes.POINTER(i64)]),
     }
@@ -262,6 +264,15 @@ class Band:
                                                int(rhs_block), 0, _ptr(s), ctypes.byref(it))
         if raise_on_fail:
             self.ctx.check(st, "bf_estimate_variance")
+        return SolveInfo(it.value, 0.0, st)
+
+    def estimate_variance_range(self, s_sum, k_begin, k_end, seed=0, rel_tol=1e-6, max_iter=20000, rhs_block=0):
+        """Partial probe sum over probes [k_begin, k_end) (bf_estimate_variance_range)."""
+        it = ctypes.c_int()
+        st = self.ctx.lib.bf_estimate_variance_range(self.ctx._p, self._p, int(k_begin), int(k_end), int(seed),
+                                                     rel_tol, max_iter, int(rhs_block), 0, _ptr(s_sum),
+                                                     ctypes.byref(it))
+        self.ctx.check(st, "bf_estimate_variance_range")
         return SolveInfo(it.value, 0.0, st)
 
     def extract_surface(self, mu, device="numpy"):

@@ -355,9 +355,28 @@ bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, do
   float* ds;
   bool host;
   BF_TRY(stage_out(ctx, s, b->N, WS_OUT1, &ds, &host));
-  bf_status st = variance_impl(ctx, b, K, seed, rel_tol, max_iter, rhs_block, flags, ds, total_iters);
+  bf_status st = variance_impl(ctx, b, 0, K, 1.0 / K, seed, rel_tol, max_iter, rhs_block, flags, ds, total_iters);
   if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
     bf_status c = copy_out(ctx, s, (const float*)ds, b->N, host);
+    if (c != BF_OK) return c;
+  }
+  return st;
+}
+
+bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* b, int k_begin, int k_end, uint64_t seed, double rel_tol,
+                                     int max_iter, int rhs_block, unsigned flags, float* s_sum, int* total_iters) {
+  if (!ctx || !b || !s_sum) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_estimate_variance_range: call bf_integrate_depth first");
+  if (k_begin < 0 || k_end <= k_begin || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: need 0 <= k_begin < k_end, 0 < rel_tol < 1");
+  if (rhs_block != 0 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: rhs_block must be 0, 8, 16 or 32");
+  float* ds;
+  bool host;
+  BF_TRY(stage_out(ctx, s_sum, b->N, WS_OUT1, &ds, &host));
+  bf_status st = variance_impl(ctx, b, k_begin, k_end, 1.0, seed, rel_tol, max_iter, rhs_block, flags, ds, total_iters);
+  if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
+    bf_status c = copy_out(ctx, s_sum, (const float*)ds, b->N, host);
     if (c != BF_OK) return c;
   }
   return st;

@@ -685,7 +685,8 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
 }
 
 template <int R>
-static bf_status variance_t(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, double tol, int max_iter, float* s_out,
+static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
+                            int max_iter, float* s_out,
                             int* total_iters) {
   cudaStream_t s = ctx->stream;
   BlockGraph* g = nullptr;
@@ -705,9 +706,9 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, doubl
   bf_status result = BF_OK;
   const int64_t NR = (int64_t)N * R;
   const unsigned gNR = grid_for(NR, 256, 152 * 32);
-  for (int k0 = 0; k0 < K; k0 += R) {
+  for (int k0 = kb; k0 < ke; k0 += R) {
     // one block of R probes: FP64 master iterates, FP32 correction solves
-    int ncols = K - k0 < R ? K - k0 : R;
+    int ncols = ke - k0 < R ? ke - k0 : R;
     k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.x64, g->h.r[0]);
     count_launch();
     k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols, N, ETA_MIN);
@@ -737,7 +738,7 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, doubl
     if (h.status == 2) { result = BF_BREAKDOWN; break; }
     if (!done || h.status == 1) { result = BF_NOT_CONVERGED; break; }
   }
-  k_finish<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->sacc, 1.0 / K, s_out);
+  k_finish<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->sacc, scale, s_out);
   count_launch();
   BF_CK(cudaGetLastError());
   BF_CK(cudaStreamSynchronize(s));
@@ -790,18 +791,20 @@ bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int which, int R, int reps, 
   return bf_fail(ctx, BF_EINVAL, "R must be 8, 16 or 32");
 }
 
-bf_status variance_impl(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, double tol, int max_iter, int R,
-                        unsigned flags, float* s, int* total_iters) {
+// probes k in [kb, ke); s = scale * sum_k z_k (.) Q^-1 z_k
+bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
+                        int max_iter, int R, unsigned flags, float* s, int* total_iters) {
   (void)flags;
   if (b->N == 0) {
     if (total_iters) *total_iters = 0;
     return BF_OK;
   }
+  const int K = ke - kb;
   if (R == 0) R = K >= 32 ? 32 : (K >= 16 ? 16 : 8);
   switch (R) {
-    case 8: return variance_t<8>(ctx, b, K, seed, tol, max_iter, s, total_iters);
-    case 16: return variance_t<16>(ctx, b, K, seed, tol, max_iter, s, total_iters);
-    case 32: return variance_t<32>(ctx, b, K, seed, tol, max_iter, s, total_iters);
+    case 8: return variance_t<8>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters);
+    case 16: return variance_t<16>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters);
+    case 32: return variance_t<32>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters);
   }
   return bf_fail(ctx, BF_EINVAL, "rhs_block must be 0, 8, 16 or 32");
 }

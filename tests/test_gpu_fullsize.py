@@ -1,0 +1,98 @@
+"""GPU parity at the benchmark's full size and launch configuration.
+
+union256: 256^3 grid at 4 mm, band +-5, 100 views 640x480 (N = 640,524 band
+voxels), FP32 PCG to rel_tol 1e-6 with 64 probes in blocks of 32 -- exactly
+what bench.py times -- against the oracle on the same inputs.
+"""
+import warnings
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import assert_band_equal, dev, gpu_band, torch
+
+pytestmark = pytest.mark.gpu
+
+TOL, K, R, SEED = 1e-6, 64, 32, 0
+
+
+@pytest.fixture(scope="module")
+def full():
+    w = synth.make_workload("union256")
+    ob = oracle.build_band_w(w)
+    d, hd, _ = oracle.integrate_w(ob, w)
+    qd, rhs = oracle.assemble(ob, d, hd, w.lam, w.lam_b)
+    mu, st, it, rr = oracle.pcg(ob, w.lam, qd, rhs, tol=1e-12)
+    assert st == 0
+    s, st, tot, _ = oracle.hutchinson(ob, w.lam, qd, K, SEED, tol=1e-12)
+    assert st == 0
+    gb, depth, poses = gpu_band(w)
+    gb.integrate_depth(depth, poses, w.intr)
+    return dict(w=w, ob=ob, d=d, hd=hd, qd=qd, rhs=rhs, mu=mu, s=s, gb=gb)
+
+
+def test_full_band_is_bit_exact(full):
+    assert full["gb"].N == 640524
+    assert_band_equal(full["gb"], full["ob"])
+
+
+def test_full_system(full):
+    sg = full["gb"].export_system()
+    for k, ref in (("d", full["d"]), ("hdata", full["hd"]), ("qdiag", full["qd"]), ("rhs", full["rhs"])):
+        np.testing.assert_allclose(sg[k], ref, rtol=1e-4, atol=2e-5 * np.abs(ref).max(), err_msg=k)
+
+
+def test_full_mean_at_bench_tolerance_and_at_1e8(full):
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+    gb, w = full["gb"], full["w"]
+    mu = torch.empty(gb.N, device="cuda")
+    info = gb.solve_mean(mu, rel_tol=TOL)
+    assert info.rel_res <= TOL
+    m = mu.cpu().numpy().astype(np.float64)
+    rp, ci, val = oracle.csr(full["ob"], w.lam, full["qd"])
+    Q = sp.csr_matrix((val, ci, rp), shape=(gb.N, gb.N))
+    r = np.linalg.norm(full["rhs"] - Q @ m)
+    # lambda_min(Q) by Jacobi-preconditioned LOBPCG; the Rayleigh quotient is an
+    # upper estimate, so the bound uses half of it
+    x0 = np.random.default_rng(0).standard_normal((gb.N, 1))
+    M = sp.diags(1.0 / full["qd"])
+    lmin = float(sla.lobpcg(Q, x0, M=M, largest=False, tol=1e-6, maxiter=500)[0][0])
+    e = np.linalg.norm(m - full["mu"])
+    ulp = np.linalg.norm(np.abs(full["mu"]) * 2.0 ** -23)
+    assert e <= r / (0.5 * lmin) + ulp, (e, r / lmin)
+    info = gb.solve_mean(mu, rel_tol=1e-8)
+    assert np.abs(mu.cpu().numpy() - full["mu"]).max() <= 1e-3
+
+
+def test_full_variance_in_bench_configuration(full):
+    gb = full["gb"]
+    s = torch.empty(gb.N, device="cuda")
+    info = gb.estimate_variance(s, K=K, seed=SEED, rel_tol=TOL, rhs_block=R)
+    assert info.iters >= K
+    rel = np.abs(s.cpu().numpy() - full["s"]) / np.maximum(np.abs(full["s"]), 1.0 / full["qd"])
+    assert rel.max() <= 1e-3, rel.max()
+
+
+def test_full_marching_cubes_topology(full):
+    mu32 = full["mu"].astype(np.float32)
+    V, F = full["gb"].extract_surface(dev(mu32))
+    Vo, Fo = oracle.marching_cubes(full["ob"], mu32)
+    assert len(F) > 100000
+    np.testing.assert_array_equal(F, Fo)
+    np.testing.assert_allclose(V, Vo, rtol=0, atol=2e-6 + 1e-5 * full["w"].h)
+
+
+def test_full_view_scores(full):
+    w, gb = full["w"], full["gb"]
+    mu32 = full["mu"].astype(np.float32)
+    s32 = full["s"].astype(np.float32)
+    qd32 = gb.export_system()["qdiag"].astype(np.float64)
+    cand = w.cand_poses[::16]
+    U, best = gb.score_views(dev(mu32), dev(s32), dev(cand), w.cand_intr)
+    Uo, besto = oracle.score_views(full["ob"], mu32, s32.astype(np.float64), qd32, cand, w.cand_intr, w.band_vox,
+                                   w.sig_a, w.sig_b, w.sig_pose, w.sig_model)
+    np.testing.assert_allclose(U, Uo, rtol=1e-3, atol=1e-6 * Uo.max())
+    assert best == besto or Uo[best] >= Uo[besto] * (1 - 1e-3)

@@ -221,3 +221,19 @@ def test_view_scores_match_oracle(name):
     assert Uo.max() > 0
     np.testing.assert_allclose(U, Uo, rtol=1e-3, atol=1e-6 * Uo.max())
     assert best == besto or Uo[best] >= Uo[besto] * (1 - 1e-3)
+
+
+def test_probe_ranges_sum_to_the_full_estimate():
+    from paper_2602_19697_gb300.sharding import estimate_variance_sharded, gpu_partial_fn
+    c = case("sphere32_small")
+    w = c["w"]
+    gb, depth, poses = gpu_band(w)
+    gb.integrate_depth(depth, poses, w.intr)
+    K = 20
+    s = torch.empty(gb.N, device="cuda")
+    gb.estimate_variance(s, K=K, seed=5, rel_tol=1e-8, rhs_block=8)
+    fn = gpu_partial_fn(gb, gb.N, seed=5, rel_tol=1e-8, rhs_block=8)
+    parts = fn(0, 7) + fn(7, 20)          # two "ranks"
+    np.testing.assert_allclose((parts / K).cpu().numpy(), s.cpu().numpy(), rtol=2e-5, atol=0)
+    one = estimate_variance_sharded(fn, K, 0, 1)   # one rank: no collective
+    np.testing.assert_allclose(one.cpu().numpy(), s.cpu().numpy(), rtol=2e-5, atol=0)

@@ -24,6 +24,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bfo.c")
+_SRC_NET = os.path.join(_HERE, "net.c")
 _LIB = os.path.join(_HERE, "_bfo.so")
 _lib = None
 
@@ -45,10 +46,11 @@ class _Band(ctypes.Structure):
 
 def build(force: bool = False) -> str:
     """Compile the oracle in-tree (gcc, FP contraction off, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_NET))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               "-fopenmp", "-std=c11", "-D_DEFAULT_SOURCE", _SRC, "-o", tmp, "-lm"])
+                               "-fopenmp", "-std=c11", "-D_DEFAULT_SOURCE", _SRC, _SRC_NET, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -86,6 +88,11 @@ def _load():
                          ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))]
     L.bfo_free.argtypes = [ctypes.c_void_p]
     L.bfo_predict_depth.argtypes = [bp, c_fp, c_fp, f, f, f, f, i, i, c_fp]
+    L.bfo_net_nparams.restype = i64
+    L.bfo_net_nparams.argtypes = []
+    L.bfo_net_features.argtypes = [bp, c_dp, c_dp]
+    L.bfo_net_loss.restype = d
+    L.bfo_net_loss.argtypes = [c_dp, i, c_dp, c_dp, ctypes.POINTER(ctypes.c_uint8), c_dp, c_dp]
     L.bfo_score_views.restype = i
     L.bfo_score_views.argtypes = [bp, c_fp, c_dp, c_dp, c_fp, i, f, f, f, f, i, i, d, d, d, d, d, d, c_dp]
     _lib = L
@@ -330,3 +337,44 @@ def solve_all(w, threads=0, tol=1e-12, K=None):
         s, st2, tot, _ = hutchinson(b, w.lam, qd, K, w.seed, tol=tol)
         out.update(s=s, hutch_iters=tot)
     return out
+
+
+# ------------------------------------------------------------ learned part
+
+def net_nparams() -> int:
+    return int(_load().bfo_net_nparams())
+
+
+def net_features(band: Band, d) -> np.ndarray:
+    """[NB,1000,2] input tiles (tsdf/h, log(1+d)) of the band's bricks."""
+    d = _f64(d)
+    feat = np.empty((band.NB, 1000, 2), np.float64)
+    _load().bfo_net_features(band._ptr, _p(d, ctypes.c_double), _p(feat, ctypes.c_double))
+    return feat
+
+
+def net_targets(band: Band, mu, log_s):
+    """Per-brick centre targets [NB,512,2] and band mask [NB,512] from compact arrays."""
+    tgt = np.zeros((band.NB, 512, 2), np.float64)
+    mask = np.zeros((band.NB, 512), np.uint8)
+    brick = np.repeat(np.arange(band.NB), np.diff(band.off))
+    ijk = band.ijk()
+    loc = (ijk[:, 0] & 7) + 8 * (ijk[:, 1] & 7) + 64 * (ijk[:, 2] & 7)
+    tgt[brick, loc, 0] = mu
+    tgt[brick, loc, 1] = log_s
+    mask[brick, loc] = 1
+    return tgt, mask
+
+
+def net_loss(params, feat, tgt, mask, grad=True):
+    """Returns (loss, grad [P] or None, pred [NB,512,2])."""
+    L = _load()
+    params, feat, tgt = _f64(params), _f64(feat), _f64(tgt)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    NB = feat.shape[0]
+    g = np.empty(len(params), np.float64) if grad else None
+    pred = np.empty((NB, 512, 2), np.float64)
+    loss = L.bfo_net_loss(_p(params, ctypes.c_double), NB, _p(feat, ctypes.c_double), _p(tgt, ctypes.c_double),
+                          _p(mask, ctypes.c_uint8), _p(g, ctypes.c_double) if grad else None,
+                          _p(pred, ctypes.c_double))
+    return loss, g, pred

@@ -950,3 +950,22 @@ int bfo_score_views(const bfo_band* B, const float* mu, const double* s, const d
   free(dd);
   return best;
 }
+
+/* ------------------------------------------- learned-part input tiles */
+
+/* Network inputs of every active brick: a 10^3 tile (brick + 1-voxel halo,
+ * tile index tx + 10 ty + 100 tz), channel 0 = tsdf/h, channel 1 =
+ * log(1 + d) at band voxels, 0 elsewhere.  feat: [NB][1000][2]. */
+void bfo_net_features(const bfo_band* B, const double* d, double* feat) {
+  for (int32_t r = 0; r < B->NB; ++r) {
+    const int* bc = B->bcoord + 3 * (int64_t)r;
+    for (int tz = 0; tz < 10; ++tz)
+      for (int ty = 0; ty < 10; ++ty)
+        for (int tx = 0; tx < 10; ++tx) {
+          int64_t v = band_index(B, 8 * bc[0] + tx - 1, 8 * bc[1] + ty - 1, 8 * bc[2] + tz - 1);
+          double* f = feat + ((int64_t)r * 1000 + tx + 10 * ty + 100 * tz) * 2;
+          f[0] = v >= 0 ? (double)B->tsdf[v] / (double)B->h : 0.0;
+          f[1] = v >= 0 ? log1p(d[v]) : 0.0;
+        }
+  }
+}

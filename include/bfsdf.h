@@ -219,6 +219,70 @@ bf_status bf_score_views(bf_ctx* ctx, const bf_band* band, const float* mu, cons
 bf_status bf_solve_mean_static(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter, float* mu, int* iters,
                                double* rel_res);
 
+/* ---- Learned warm start and variance surrogate ----------------------------
+ * The paper has no counterpart: its Sec. 6 lists learned priors as future
+ * work.  The network maps per-brick input tiles to a warm start for the mean
+ * solve and an estimate of diag(Q^-1) that replaces the probe estimate on the
+ * bricks where an independent probe judge agrees with it.
+ *   Network: per band brick a 10^3 tile (the brick and a 1-voxel halo) with
+ *   2 input channels, tsdf/h and log(1 + d) at band voxels and 0 elsewhere;
+ *   four 3x3x3 convolutions 2 -> 32 -> 32 -> 32 -> 2 with bias, zero padding
+ *   at the tile boundary, ReLU after the first three; at the brick's voxels
+ *   mu_hat = tsdf/h + o0 (voxels) and log s_hat = o1 - log Q_jj (log
+ *   voxels^2): residuals on the TSDF and on the Jacobi lower bound 1/Q_jj.
+ *   Parameters: one float vector of bf_net_nparams() = 58,850 values,
+ *   W1 b1 W2 b2 W3 b3 W4 b4 with W_l[tap][ci][co], tap = 9 (dz+1) + 3 (dy+1)
+ *   + (dx+1), b_l[co].  The library keeps an FP32 master copy and Adam
+ *   moments; the convolutions run on bf16 tensor-core operands with FP32
+ *   accumulation.
+ *   Loss over the band voxels j (M of them):
+ *   L = (1/M) sum_j (mu_hat_j - mu_j)^2 + (log s_hat_j - log max(s_j, 1/Q_jj))^2. */
+typedef struct bf_net bf_net;
+
+/* Number of network parameters (58,850). */
+int64_t bf_net_nparams(void);
+
+/* Create a network on the context's device with He-normal weights drawn from
+ * a counter-based hash of `seed` (last layer scaled by 0.1), zero biases. */
+bf_status bf_net_create(bf_ctx* ctx, uint64_t seed, bf_net** net);
+void bf_net_destroy(bf_net* net);
+
+/* Copy the FP32 parameters out / in ([nparams] floats, host or device).
+ * Setting parameters resets the Adam moments and step count. */
+bf_status bf_net_get_params(bf_ctx* ctx, const bf_net* net, float* params);
+bf_status bf_net_set_params(bf_ctx* ctx, bf_net* net, const float* params);
+
+/* Inference over the band (after bf_integrate_depth): mu_hat [N] float
+ * (voxels; pass it to bf_solve_mean with BF_SOLVE_WARM as the initial guess)
+ * and log_s_hat [N] float (pass it to bf_surrogate_variance). */
+bf_status bf_net_forward(bf_ctx* ctx, bf_net* net, const bf_band* band, float* mu_hat, float* log_s_hat);
+
+/* One training step on one band: forward, loss L (above) against targets
+ * mu [N] float (voxels) and s [N] float (voxels^2; the fitted value is
+ * log max(s, 1/Q_jj)), backward, then one Adam step (beta 0.9, 0.999,
+ * eps 1e-8) with learning rate lr (0 = gradient only).  *loss (host, may be
+ * NULL) receives L before the update; grad [nparams] float (may be NULL)
+ * receives dL/dparams. */
+bf_status bf_net_train_step(bf_ctx* ctx, bf_net* net, const bf_band* band, const float* mu, const float* s,
+                            float lr, double* loss, float* grad);
+
+/* diag(Q^-1) with the network's estimate where a probe judge accepts it.
+ * The judge is the estimator of bf_estimate_variance restricted to probes
+ * 0 .. K_judge-1 of `seed`: per voxel s_J (mean of the K_judge probe values
+ * t_k = z_k (.) Q^-1 z_k), its standard error se (sample std / sqrt(K_judge)),
+ * f = max(s_J, 1/Q_jj) and e = |exp(log_s_hat) - s_J|.  A brick is accepted
+ * when the median over its voxels of e/f is <= 0.10 (brick_stat[b][0]) and
+ * no voxel has e > 3 se + 0.1 f (brick_stat[b][1] = max e / (3 se + 0.1 f)
+ * <= 1).  Output s [N] float: exp(log_s_hat) on accepted bricks; elsewhere
+ * the K-probe estimate of bf_estimate_variance(K, seed), for which the
+ * remaining probes K_judge .. K-1 are solved only if some brick is rejected.
+ * accepted [NB] uint8 and brick_stat [NB][2] double may be NULL;
+ * *n_accepted and *total_iters (host, may be NULL) receive the number of
+ * accepted bricks and the summed probe iterations.  Needs 2 <= K_judge < K. */
+bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* band, const float* log_s_hat, int K, int K_judge,
+                                uint64_t seed, double rel_tol, int max_iter, int rhs_block, unsigned flags, float* s,
+                                uint8_t* accepted, double* brick_stat, int* n_accepted, int* total_iters);
+
 /* Kernel timing for roofline measurements: launches kernels of the solver
  * `reps` times back to back on the context stream between two CUDA events
  * and returns the mean time per repetition (ms).

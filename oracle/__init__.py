@@ -7,7 +7,9 @@ Python binding) never imports, links or runs it, and the two share no code.
 The arithmetic lives in ``bfo.c`` (plain C, FP64 for every real-valued
 quantity, a fixed FP32 specification for discrete decisions; every function
 there cites the section of the paper it restates).  This module compiles it
-with gcc and marshals numpy arrays through ctypes; it computes nothing.
+with gcc and marshals numpy arrays through ctypes; the one function written
+here in numpy is ``surrogate_judge`` (a per-brick statistic over values the C
+code returns).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests against
 closed forms, invariants, special cases or brute force (see
@@ -16,6 +18,7 @@ tests/test_oracle_*.py); none is "parity unpinned".
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 from dataclasses import dataclass
@@ -92,7 +95,7 @@ def _load():
     L.bfo_net_nparams.argtypes = []
     L.bfo_net_features.argtypes = [bp, c_dp, c_dp]
     L.bfo_net_loss.restype = d
-    L.bfo_net_loss.argtypes = [c_dp, i, c_dp, c_dp, ctypes.POINTER(ctypes.c_uint8), c_dp, c_dp]
+    L.bfo_net_loss.argtypes = [c_dp, i, c_dp, c_dp, c_dp, ctypes.POINTER(ctypes.c_uint8), c_dp, c_dp]
     L.bfo_score_views.restype = i
     L.bfo_score_views.argtypes = [bp, c_fp, c_dp, c_dp, c_fp, i, f, f, f, f, i, i, d, d, d, d, d, d, c_dp]
     _lib = L
@@ -353,28 +356,58 @@ def net_features(band: Band, d) -> np.ndarray:
     return feat
 
 
-def net_targets(band: Band, mu, log_s):
-    """Per-brick centre targets [NB,512,2] and band mask [NB,512] from compact arrays."""
+def net_targets(band: Band, mu, log_s, qdiag=None):
+    """Per-brick centre arrays from compact ones: targets [NB,512,2] (mu, log s),
+    band mask [NB,512] and log Q_ii [NB,512] (0 where qdiag is None or off the band)."""
     tgt = np.zeros((band.NB, 512, 2), np.float64)
     mask = np.zeros((band.NB, 512), np.uint8)
+    lq = np.zeros((band.NB, 512), np.float64)
     brick = np.repeat(np.arange(band.NB), np.diff(band.off))
     ijk = band.ijk()
     loc = (ijk[:, 0] & 7) + 8 * (ijk[:, 1] & 7) + 64 * (ijk[:, 2] & 7)
     tgt[brick, loc, 0] = mu
     tgt[brick, loc, 1] = log_s
     mask[brick, loc] = 1
-    return tgt, mask
+    if qdiag is not None:
+        lq[brick, loc] = np.log(np.asarray(qdiag, np.float64))
+    return tgt, mask, lq
 
 
-def net_loss(params, feat, tgt, mask, grad=True):
-    """Returns (loss, grad [P] or None, pred [NB,512,2])."""
+def net_loss(params, feat, tgt, mask, lq=None, grad=True):
+    """Returns (loss, grad [P] or None, pred [NB,512,2]); lq [NB,512] log Q_ii (default 0)."""
     L = _load()
     params, feat, tgt = _f64(params), _f64(feat), _f64(tgt)
     mask = np.ascontiguousarray(mask, np.uint8)
     NB = feat.shape[0]
+    lq = np.zeros((NB, 512)) if lq is None else lq
+    lq = _f64(lq)
     g = np.empty(len(params), np.float64) if grad else None
     pred = np.empty((NB, 512, 2), np.float64)
-    loss = L.bfo_net_loss(_p(params, ctypes.c_double), NB, _p(feat, ctypes.c_double), _p(tgt, ctypes.c_double),
-                          _p(mask, ctypes.c_uint8), _p(g, ctypes.c_double) if grad else None,
+    loss = L.bfo_net_loss(_p(params, ctypes.c_double), NB, _p(feat, ctypes.c_double), _p(lq, ctypes.c_double),
+                          _p(tgt, ctypes.c_double), _p(mask, ctypes.c_uint8), _p(g, ctypes.c_double) if grad else None,
                           _p(pred, ctypes.c_double))
     return loss, g, pred
+
+
+def surrogate_judge(band: Band, log_s_hat, t, qdiag):
+    """Acceptance test of the learned variance surrogate, per brick.
+
+    t [K_j, N]: per-probe values t_k = z_k (.) Q^-1 z_k of K_j probes.  With
+    s_J = mean_k t_k, se = sample std / sqrt(K_j), f = max(s_J, 1/Q_ii) and
+    e = |exp(log_s_hat) - s_J|, a brick is accepted when the median of e/f
+    over its voxels is <= 0.10 and max e / (3 se + 0.1 f) <= 1.
+    Returns (stat [NB, 2] = (median, max ratio), accepted [NB] uint8)."""
+    t = np.asarray(t, np.float64)
+    Kj = t.shape[0]
+    sJ = t.mean(axis=0)
+    se = t.std(axis=0, ddof=1) / math.sqrt(Kj)
+    f = np.maximum(sJ, 1.0 / np.asarray(qdiag, np.float64))
+    e = np.abs(np.exp(np.asarray(log_s_hat, np.float64)) - sJ)
+    stat = np.zeros((band.NB, 2))
+    acc = np.zeros(band.NB, np.uint8)
+    for b in range(band.NB):
+        sl = slice(band.off[b], band.off[b + 1])
+        stat[b, 0] = np.median(e[sl] / f[sl])
+        stat[b, 1] = np.max(e[sl] / (3.0 * se[sl] + 0.1 * f[sl]))
+        acc[b] = stat[b, 0] <= 0.10 and stat[b, 1] <= 1.0
+    return stat, acc

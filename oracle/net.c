@@ -10,7 +10,10 @@
  *   layers  four 3x3x3 convolutions 2 -> 32 -> 32 -> 32 -> 2 with bias,
  *           zero padding at the tile boundary ("same" size 10^3), ReLU after
  *           the first three;
- *   output  at the 8^3 centre: mu_hat = tsdf/h + o0 (voxels) and log s_hat = o1;
+ *   output  at the 8^3 centre: mu_hat = tsdf/h + o0 (voxels) and
+ *           log s_hat = o1 - log Q_ii (both outputs are residuals on a
+ *           closed-form baseline: the TSDF, and the Jacobi value 1/Q_ii that
+ *           bounds (Q^-1)_ii from below for SPD Q);
  *   loss    L = (1/M) sum over band voxels of (mu_hat - mu)^2 + (log s_hat - log s)^2.
  * Weights W_l[tap][ci][co], tap = (dz+1) 9 + (dy+1) 3 + (dx+1), then b_l[co];
  * the flat parameter vector is W1 b1 W2 b2 W3 b3 W4 b4.
@@ -55,12 +58,13 @@ static void conv_fwd(const double* W, const double* b, int ci_n, int co_n, const
 
 /*
  * Loss, gradient and predictions over NB brick tiles.
- *   feat [NB][1000][2] inputs; tgt [NB][512][2] targets (mu, log s) at the
- *   centre voxels (local index lx + 8 ly + 64 lz); mask [NB][512] 1 = band.
- *   grad [P] (may be NULL); pred [NB][512][2] (may be NULL).
+ *   feat [NB][1000][2] inputs; lq [NB][512] log Q_ii at the centre voxels
+ *   (local index lx + 8 ly + 64 lz); tgt [NB][512][2] targets (mu, log s);
+ *   mask [NB][512] 1 = band.  grad [P] (may be NULL); pred [NB][512][2]
+ *   (may be NULL).
  */
-double bfo_net_loss(const double* params, int NB, const double* feat, const double* tgt, const uint8_t* mask,
-                    double* grad, double* pred) {
+double bfo_net_loss(const double* params, int NB, const double* feat, const double* lq, const double* tgt,
+                    const uint8_t* mask, double* grad, double* pred) {
   const double* W[4];
   const double* B[4];
   int64_t off = 0;
@@ -101,7 +105,7 @@ double bfo_net_loss(const double* params, int NB, const double* feat, const doub
       for (int ly = 0; ly < 8; ++ly)
         for (int lx = 0; lx < 8; ++lx) {
           int loc = lx + 8 * ly + 64 * lz, v = (lx + 1) + 10 * (ly + 1) + 100 * (lz + 1);
-          double mh = x0[v * 2] + act[4][v * 2], lh = act[4][v * 2 + 1];
+          double mh = x0[v * 2] + act[4][v * 2], lh = act[4][v * 2 + 1] - lq[(int64_t)b * 512 + loc];
           if (pred) {
             pred[((int64_t)b * 512 + loc) * 2] = mh;
             pred[((int64_t)b * 512 + loc) * 2 + 1] = lh;

@@ -32,7 +32,8 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_band_info", "bf_export_band", "bf_integrate_depth", "bf_reset_observations", "bf_export_system",
             "bf_spmv", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
             "bf_score_views", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
-            "bf_launch_count"]
+            "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
+            "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance"]
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
 BF_KERNEL_BLOCK_UPDATE = 2
@@ -97,6 +98,15 @@ def load_library(path: str = LIB_PATH):
         "bf_estimate_variance_range": (i, [vp, vp, i, i, ctypes.c_uint64, d, i, i, u, vp, ctypes.POINTER(i)]),
         "bf_bench_kernel": (i, [vp, vp, i, i, i, ctypes.POINTER(d)]),
         "bf_launch_count": (i, [ctypes.POINTER(i64)]),
+        "bf_net_nparams": (i64, []),
+        "bf_net_create": (i, [vp, ctypes.c_uint64, pvp]),
+        "bf_net_destroy": (None, [vp]),
+        "bf_net_get_params": (i, [vp, vp, vp]),
+        "bf_net_set_params": (i, [vp, vp, vp]),
+        "bf_net_forward": (i, [vp, vp, vp, vp, vp]),
+        "bf_net_train_step": (i, [vp, vp, vp, vp, vp, ctypes.c_float, ctypes.POINTER(d), vp]),
+        "bf_surrogate_variance": (i, [vp, vp, vp, i, i, ctypes.c_uint64, d, i, i, u, vp, vp, vp,
+                                      ctypes.POINTER(i), ctypes.POINTER(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -275,6 +285,19 @@ class Band:
         self.ctx.check(st, "bf_estimate_variance_range")
         return SolveInfo(it.value, 0.0, st)
 
+    def surrogate_variance(self, log_s_hat, s, K, K_judge=16, seed=0, rel_tol=1e-6, max_iter=20000, rhs_block=0):
+        """diag(Q^-1) with the network's estimate on judge-accepted bricks (bf_surrogate_variance).
+
+        Returns (SolveInfo, accepted [NB] uint8, brick_stat [NB, 2] float64, n_accepted)."""
+        it, na = ctypes.c_int(), ctypes.c_int()
+        acc = np.zeros(self.NB, np.uint8)
+        stat = np.zeros((self.NB, 2), np.float64)
+        st = self.ctx.lib.bf_surrogate_variance(self.ctx._p, self._p, _ptr(log_s_hat), int(K), int(K_judge),
+                                                int(seed), rel_tol, max_iter, int(rhs_block), 0, _ptr(s),
+                                                _ptr(acc), _ptr(stat), ctypes.byref(na), ctypes.byref(it))
+        self.ctx.check(st, "bf_surrogate_variance")
+        return SolveInfo(it.value, 0.0, st), acc, stat, na.value
+
     def extract_surface(self, mu, device="numpy"):
         nv, nt = ctypes.c_int64(), ctypes.c_int64()
         self.ctx.check(self.ctx.lib.bf_extract_surface(self.ctx._p, self._p, _ptr(mu), ctypes.byref(nv),
@@ -300,3 +323,48 @@ class Band:
         self.ctx.check(self.ctx.lib.bf_bench_kernel(self.ctx._p, self._p, int(which), int(R), int(reps),
                                                     ctypes.byref(ms)), "bf_bench_kernel")
         return ms.value
+
+
+def net_nparams() -> int:
+    return int(load_library().bf_net_nparams())
+
+
+class Net:
+    """The learned warm start / variance surrogate network (bf_net_*)."""
+
+    def __init__(self, ctx: Context, seed: int = 0):
+        self.ctx = ctx
+        p = ctypes.c_void_p()
+        ctx.check(ctx.lib.bf_net_create(ctx._p, int(seed), ctypes.byref(p)), "bf_net_create")
+        self._p = p
+        self.P = net_nparams()
+
+    def close(self):
+        if self._p:
+            self.ctx.lib.bf_net_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self, out=None):
+        out = np.empty(self.P, np.float32) if out is None else out
+        self.ctx.check(self.ctx.lib.bf_net_get_params(self.ctx._p, self._p, _ptr(out)), "bf_net_get_params")
+        return out
+
+    def set_params(self, params):
+        self.ctx.check(self.ctx.lib.bf_net_set_params(self.ctx._p, self._p, _ptr(params)), "bf_net_set_params")
+
+    def forward(self, band: "Band", mu_hat, log_s_hat):
+        self.ctx.check(self.ctx.lib.bf_net_forward(self.ctx._p, self._p, band._p, _ptr(mu_hat), _ptr(log_s_hat)),
+                       "bf_net_forward")
+
+    def train_step(self, band: "Band", mu, s, lr=1e-3, grad=None) -> float:
+        loss = ctypes.c_double()
+        self.ctx.check(self.ctx.lib.bf_net_train_step(self.ctx._p, self._p, band._p, _ptr(mu), _ptr(s),
+                                                      float(lr), ctypes.byref(loss), _ptr(grad)),
+                       "bf_net_train_step")
+        return loss.value

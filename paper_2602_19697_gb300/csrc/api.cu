@@ -69,44 +69,6 @@ void* ws_get(bf_ctx* ctx, int slot, size_t bytes, bf_status* st) {
 
 namespace {
 
-// Device view of a caller array: the array itself if it is device memory,
-// else a staged copy in workspace slot `slot`.
-template <class T>
-bf_status stage_in(bf_ctx* ctx, const T* p, size_t count, int slot, const T** out) {
-  if (is_device_ptr(p)) {
-    *out = p;
-    return BF_OK;
-  }
-  bf_status st;
-  T* d = (T*)ws_get(ctx, slot, count * sizeof(T), &st);
-  if (st) return st;
-  BF_CK(cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
-  *out = d;
-  return BF_OK;
-}
-
-// Output target: the caller array if device memory, else a workspace buffer
-// that copy_out writes back.
-template <class T>
-bf_status stage_out(bf_ctx* ctx, T* p, size_t count, int slot, T** out, bool* host) {
-  *host = !is_device_ptr(p);
-  if (!*host) {
-    *out = p;
-    return BF_OK;
-  }
-  bf_status st;
-  *out = (T*)ws_get(ctx, slot, count * sizeof(T), &st);
-  return st;
-}
-
-template <class T>
-bf_status copy_out(bf_ctx* ctx, T* user, const T* dev, size_t count, bool host) {
-  if (!host) return BF_OK;
-  BF_CK(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
-  BF_CK(cudaStreamSynchronize(ctx->stream));
-  return BF_OK;
-}
-
 __global__ void k_i32_to_i64(const int32_t* in, int64_t* out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = in[i];

@@ -467,15 +467,20 @@ __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed,
   }
 }
 
-// s_acc[i] += sum_c z[i][c] x64[i][c]
+// s_acc[i] += sum_c z[i][c] x64[i][c]; sq[i] += sum_c (z[i][c] x64[i][c])^2 if sq
 template <int R>
 __global__ void k_hutch(int N, const __nv_bfloat16* __restrict__ Z, const double* __restrict__ x,
-                        double* __restrict__ sacc) {
+                        double* __restrict__ sacc, double* __restrict__ sq) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    double s = 0.0;
+    double s = 0.0, q = 0.0;
 #pragma unroll
-    for (int c = 0; c < R; ++c) s += (double)__bfloat162float(Z[(size_t)i * R + c]) * x[(size_t)i * R + c];
+    for (int c = 0; c < R; ++c) {
+      const double t = (double)__bfloat162float(Z[(size_t)i * R + c]) * x[(size_t)i * R + c];
+      s += t;
+      q += t * t;
+    }
     sacc[i] += s;
+    if (sq) sq[i] += q;
   }
 }
 
@@ -686,8 +691,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
 
 template <int R>
 static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
-                            int max_iter, float* s_out,
-                            int* total_iters) {
+                            int max_iter, float* s_out, int* total_iters, double* sq) {
   cudaStream_t s = ctx->stream;
   BlockGraph* g = nullptr;
   BF_TRY(get_block_solver<R>(ctx, b, &g));
@@ -732,7 +736,7 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
     const BlkState& h = *g->h_st;
     count_launch(h.nexec);
     for (int c = 0; c < ncols; ++c) tot_it += h.iters[c];
-    k_hutch<R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->Z, g->h.x64, g->sacc);
+    k_hutch<R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->Z, g->h.x64, g->sacc, sq);
     count_launch();
     BF_CK(cudaGetLastError());
     if (h.status == 2) { result = BF_BREAKDOWN; break; }
@@ -791,9 +795,10 @@ bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int which, int R, int reps, 
   return bf_fail(ctx, BF_EINVAL, "R must be 8, 16 or 32");
 }
 
-// probes k in [kb, ke); s = scale * sum_k z_k (.) Q^-1 z_k
+// probes k in [kb, ke); s = scale * sum_k z_k (.) Q^-1 z_k; sq (device, may be
+// null) += sum_k (z_k (.) Q^-1 z_k)^2
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
-                        int max_iter, int R, unsigned flags, float* s, int* total_iters) {
+                        int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq) {
   (void)flags;
   if (b->N == 0) {
     if (total_iters) *total_iters = 0;
@@ -802,9 +807,9 @@ bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, u
   const int K = ke - kb;
   if (R == 0) R = K >= 32 ? 32 : (K >= 16 ? 16 : 8);
   switch (R) {
-    case 8: return variance_t<8>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters);
-    case 16: return variance_t<16>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters);
-    case 32: return variance_t<32>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters);
+    case 8: return variance_t<8>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq);
+    case 16: return variance_t<16>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq);
+    case 32: return variance_t<32>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq);
   }
   return bf_fail(ctx, BF_EINVAL, "rhs_block must be 0, 8, 16 or 32");
 }

@@ -112,6 +112,44 @@ inline bf_status dev_alloc_t(bf_ctx* ctx, T** p, size_t count) {
 }
 void dev_free(cudaStream_t s, void* p);
 
+// Device view of a caller array: the array itself if it is device memory,
+// else a staged copy in workspace slot `slot`.
+template <class T>
+inline bf_status stage_in(bf_ctx* ctx, const T* p, size_t count, int slot, const T** out) {
+  if (is_device_ptr(p)) {
+    *out = p;
+    return BF_OK;
+  }
+  bf_status st;
+  T* d = (T*)ws_get(ctx, slot, count * sizeof(T), &st);
+  if (st) return st;
+  BF_CK(cudaMemcpyAsync(d, p, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  *out = d;
+  return BF_OK;
+}
+
+// Output target: the caller array if device memory, else a workspace buffer
+// that copy_out writes back.
+template <class T>
+inline bf_status stage_out(bf_ctx* ctx, T* p, size_t count, int slot, T** out, bool* host) {
+  *host = !is_device_ptr(p);
+  if (!*host) {
+    *out = p;
+    return BF_OK;
+  }
+  bf_status st;
+  *out = (T*)ws_get(ctx, slot, count * sizeof(T), &st);
+  return st;
+}
+
+template <class T>
+inline bf_status copy_out(bf_ctx* ctx, T* user, const T* dev, size_t count, bool host) {
+  if (!host) return BF_OK;
+  BF_CK(cudaMemcpyAsync(user, dev, count * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+  BF_CK(cudaStreamSynchronize(ctx->stream));
+  return BF_OK;
+}
+
 // Exclusive prefix sum of n int32 values (in and out may alias); *total
 // (device, may be null) receives the sum.
 bf_status scan_i32(bf_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, int32_t* total);
@@ -125,7 +163,7 @@ bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
 bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,
                           double* relres);
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
-                        int max_iter, int R, unsigned flags, float* s, int* total_iters);
+                        int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq = nullptr);
 bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms);
 void solve_graph_free(SolveGraph* g);
 void block_graph_free(BlockGraph* g);

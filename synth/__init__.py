@@ -99,8 +99,8 @@ def fibonacci_sphere(n: int, zmin: float = -1.0) -> np.ndarray:
     return np.stack([r * np.cos(ph), r * np.sin(ph), z], 1)
 
 
-def ring_poses(n: int, radius: float, z: float = 0.0) -> np.ndarray:
-    a = 2 * math.pi * np.arange(n) / n
+def ring_poses(n: int, radius: float, z: float = 0.0, phase: float = 0.0) -> np.ndarray:
+    a = phase + 2 * math.pi * np.arange(n) / n
     return np.stack([look_at((radius * math.cos(t), radius * math.sin(t), z)) for t in a])
 
 
@@ -213,14 +213,28 @@ def _grid(n: int, h: float):
 
 def make_workload(name: str, *, n: int | None = None, frames: int | None = None,
                   image_scale: float = 1.0, noise: bool = True, seed: int = 0,
-                  band_vox: float | None = None, threads: int = 0, n_cand: int = 64) -> Workload:
+                  band_vox: float | None = None, threads: int = 0, n_cand: int = 64,
+                  variant: int | None = None) -> Workload:
     """Build one of the named workloads.  ``n``, ``frames`` and ``image_scale``
-    shrink it for fast tests (the voxel size scales so the scene still fits)."""
+    shrink it for fast tests (the voxel size scales so the scene still fits).
+
+    ``variant`` (sphere workloads only) draws one instance of the family used
+    to train the learned warm start: sphere radius U(0.22, 0.34) m, centre
+    offset U(-0.03, 0.03) m per axis and ring phase U(0, 2 pi / frames) from
+    a generator seeded by the variant number, which is also the noise seed."""
     if name in ("sphere64", "sphere64_k256"):
         n0, h0, b, tc = 64, 0.015, 4.0, 6.0
-        scene = sphere_scene(0.3)
         T = frames or 20
-        P = ring_poses(T, 1.0)
+        if variant is None:
+            scene = sphere_scene(0.3)
+            P = ring_poses(T, 1.0)
+        else:
+            g = np.random.Generator(np.random.PCG64(10007 + int(variant)))
+            r = float(g.uniform(0.22, 0.34))
+            c = tuple(float(x) for x in g.uniform(-0.03, 0.03, 3))
+            scene = sphere_scene(r, c)
+            P = ring_poses(T, 1.0, phase=float(g.uniform(0.0, 2 * math.pi / T)))
+            seed = int(variant)
         W, H, f = 160, 120, 140.0
         sa, sb, drop, sp = 0.002, 0.004, 0.0, 0.0
         cand_r = 1.0
@@ -247,6 +261,8 @@ def make_workload(name: str, *, n: int | None = None, frames: int | None = None,
         K, tol, fp64 = 128, 1e-6, False
     else:
         raise ValueError(f"unknown workload {name!r}")
+    if variant is not None and not name.startswith("sphere"):
+        raise ValueError("variant applies to the sphere workloads only")
     if band_vox is not None and name != "blob512":
         b, tc = float(band_vox), float(band_vox) + 2.0
     nn = n or n0

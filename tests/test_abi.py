@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     hdr = open(os.path.join(ROOT, "include", "bfsdf.h")).read()
-    return re.findall(r"^(?:bf_status|void|const char\*)\s+(bf_\w+)\(", hdr, re.M)
+    return re.findall(r"^(?:bf_status|void|int64_t|const char\*)\s+(bf_\w+)\(", hdr, re.M)
 
 
 def test_library_exports_every_declared_entry_point():

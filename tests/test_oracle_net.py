@@ -44,13 +44,23 @@ def test_output_is_a_residual_on_the_tsdf_and_loss_vanishes_at_the_prediction():
     tgt = rng.standard_normal((2, 512, 2))
     mask = np.ones((2, 512), np.uint8)
     loss, g, pred = oracle.net_loss(P, feat, tgt, mask)
-    # zero weights: mu_hat = tsdf/h at the centre voxel, log s_hat = 0
+    # zero weights: mu_hat = tsdf/h at the centre voxel, log s_hat = 0 - log Q_ii
     c = np.array([(lx + 1) + 10 * (ly + 1) + 100 * (lz + 1) for lz in range(8) for ly in range(8) for lx in range(8)])
     np.testing.assert_array_equal(pred[:, :, 0], feat[:, c, 0])
     np.testing.assert_array_equal(pred[:, :, 1], 0.0)
+    lq = rng.uniform(0.0, 3.0, (2, 512))
+    _, _, pred = oracle.net_loss(P, feat, tgt, mask, lq=lq)
+    np.testing.assert_array_equal(pred[:, :, 1], -lq)
+    # the baselines shift the outputs only: the gradient is unchanged when the targets shift with them
     P = _params(4)
-    _, _, pred = oracle.net_loss(P, feat, tgt, mask, grad=False)
-    loss, g, _ = oracle.net_loss(P, feat, pred, mask)
+    _, g0, p0 = oracle.net_loss(P, feat, tgt, mask)
+    t1 = tgt.copy()
+    t1[:, :, 1] -= lq
+    _, g1, p1 = oracle.net_loss(P, feat, t1, mask, lq=lq)
+    np.testing.assert_allclose(p1[:, :, 1], p0[:, :, 1] - lq, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g1, g0, rtol=1e-9, atol=1e-12)
+    _, _, pred = oracle.net_loss(P, feat, tgt, mask, lq=lq, grad=False)
+    loss, g, _ = oracle.net_loss(P, feat, pred, mask, lq=lq)
     assert loss == 0.0 and np.all(g == 0)
 
 
@@ -67,3 +77,43 @@ def test_features_read_the_band():
         assert feat[r, t, 0] == np.float64(b.tsdf[v]) / np.float64(np.float32(b.h))
         assert feat[r, t, 1] == np.log1p(d[v])
     assert np.count_nonzero(feat[:, :, 1]) <= 1000 * b.NB
+
+
+class _Bricks:
+    """Stand-in for a band: the judge reads only NB and the brick offsets."""
+
+    def __init__(self, off):
+        self.off = np.asarray(off, np.int64)
+        self.NB = len(off) - 1
+
+
+def test_surrogate_judge_by_hand():
+    # brick 0: voxels 0-2, brick 1: voxels 3-6; two probes
+    t = np.array([[1.0, 2.0, 3.0, 4.0, 4.0, 1.0, 0.5],
+                  [3.0, 2.0, 1.0, 4.0, 4.0, 1.0, 0.5]])
+    qd = np.full(7, 1e6)
+    s_hat = np.array([2.0, 2.1, 5.0, 4.0, 4.8, 1.0, 0.5])
+    stat, acc = oracle.surrogate_judge(_Bricks([0, 3, 7]), np.log(s_hat), t, qd)
+    # brick 0: s_J = 2, se = (1, 0, 1), e / f = (0, 0.05, 1.5), e / (3 se + 0.2) = (0, 0.5, 3 / 3.2)
+    np.testing.assert_allclose(stat[0], [0.05, 3.0 / 3.2], rtol=1e-12)
+    assert acc[0] == 1
+    # brick 1: se = 0, e / f = (0, 0.2, 0, 0): median of an even count = mean of the middle two = 0;
+    # voxel 4 has e = 0.8 > 3 se + 0.1 f = 0.4
+    np.testing.assert_allclose(stat[1], [0.0, 2.0], rtol=1e-12, atol=1e-15)
+    assert acc[1] == 0
+
+
+def test_surrogate_judge_accepts_its_own_mean_and_floors_at_the_diagonal():
+    rng = np.random.default_rng(3)
+    t = rng.normal(1.0, 0.5, (16, 40))
+    qd = np.full(40, 2.0)
+    sJ = t.mean(0)
+    stat, acc = oracle.surrogate_judge(_Bricks([0, 10, 25, 40]), np.log(np.maximum(sJ, 1e-300)), t, qd)
+    pos = sJ > 0
+    assert pos.all()
+    np.testing.assert_allclose(stat, 0.0, atol=1e-12)
+    assert acc.all()
+    # a negative probe mean is floored at 1/Q_ii = 0.5: s_hat = 0.5 is then e / f = (0.5 - s_J) / 0.5
+    t2 = np.array([[-1.0], [0.6]])
+    stat2, _ = oracle.surrogate_judge(_Bricks([0, 1]), np.log([0.5]), t2, np.array([2.0]))
+    np.testing.assert_allclose(stat2[0, 0], (0.5 + 0.2) / 0.5, rtol=1e-12)

@@ -33,11 +33,16 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_spmv", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
             "bf_score_views", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
             "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
-            "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance"]
+            "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance",
+            "bf_net_bench"]
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
 BF_KERNEL_BLOCK_UPDATE = 2
 BF_KERNEL_BLOCK_SPMM = 3
+BF_NET_BENCH_FORWARD, BF_NET_BENCH_TRAIN, BF_NET_BENCH_CONV, BF_NET_BENCH_WGRAD = range(4)
+# algorithmic FLOPs of the network per brick tile (10^3 voxels, 27 taps, real channels)
+NET_FLOPS_FWD = 2 * 1000 * 27 * (2 * 32 + 32 * 32 + 32 * 32 + 32 * 2)
+NET_FLOPS_CONV = 2 * 1000 * 27 * 32 * 32
 
 
 class BfError(RuntimeError):
@@ -107,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         "bf_net_train_step": (i, [vp, vp, vp, vp, vp, ctypes.c_float, ctypes.POINTER(d), vp]),
         "bf_surrogate_variance": (i, [vp, vp, vp, i, i, ctypes.c_uint64, d, i, i, u, vp, vp, vp,
                                       ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "bf_net_bench": (i, [vp, vp, vp, i, i, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -361,6 +367,13 @@ class Net:
     def forward(self, band: "Band", mu_hat, log_s_hat):
         self.ctx.check(self.ctx.lib.bf_net_forward(self.ctx._p, self._p, band._p, _ptr(mu_hat), _ptr(log_s_hat)),
                        "bf_net_forward")
+
+    def bench(self, band: "Band", which: int, reps: int = 20) -> float:
+        """Mean ms per repetition of the network's kernels (bf_net_bench)."""
+        ms = ctypes.c_double()
+        self.ctx.check(self.ctx.lib.bf_net_bench(self.ctx._p, self._p, band._p, int(which), int(reps),
+                                                 ctypes.byref(ms)), "bf_net_bench")
+        return ms.value
 
     def train_step(self, band: "Band", mu, s, lr=1e-3, grad=None) -> float:
         loss = ctypes.c_double()

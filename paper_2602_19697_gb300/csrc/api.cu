@@ -182,7 +182,7 @@ void bf_band_free(bf_band* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   void* ptrs[] = {b->dir, b->bcoord, b->meta, b->off, b->nbr, b->lin, b->tsdf, b->wcount, b->info,
-                  b->d, b->hd, b->qd, b->rhs, b->nb6};
+                  b->d, b->hd, b->qd, b->rhs, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;

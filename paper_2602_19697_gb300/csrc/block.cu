@@ -31,6 +31,7 @@
 // The solver (workspaces, state, graph) belongs to the context, one per
 // block width R: kernels read band pointers and sizes from a device-resident
 // argument block, so the captured graph serves every band.
+#include <climits>
 #include <cstring>
 
 #include "internal.cuh"
@@ -45,6 +46,13 @@ constexpr int CT = 512;   // threads per CTA of the row kernels
 // (the FP32 recursive residual keeps falling below the true one's floor)
 constexpr double ETA_MIN = 1e-7;
 constexpr int NCTA = 152 * 2;
+// SpMM pass: tiles of SP_TR rows plus at most SP_EMAX external rows staged in
+// shared memory (SP_ROWS rows); SP_GLOBAL marks a neighbour read from global
+// memory (a tile whose external rows overflow the list)
+constexpr int SP_TR = 256, SP_EMAX = 384, SP_ROWS = SP_TR + SP_EMAX;
+constexpr int16_t SP_GLOBAL = 32767;
+constexpr int SP_NCTA = 152 * 2;
+constexpr int NPART = SP_NCTA > NCTA ? SP_NCTA : NCTA;
 
 struct BlkState {
   double alpha[MAXR], beta[MAXR], gamma[MAXR], rr[MAXR], bb[MAXR], tol2[MAXR];
@@ -62,6 +70,9 @@ struct BlkArgs {
   int N;
   float lam;
   const int32_t* nb6;  // [N][6] face-neighbour indices, -1 outside the band
+  const int32_t* sp_ext;   // [tiles][SP_EMAX] sorted external rows of each SpMM tile
+  const int32_t* sp_ne;    // [tiles] their count
+  const int16_t* sp_slot;  // [N][8] staged slot of each face neighbour (6 used)
   const float* qd;     // [N] Q_jj
   float* iq;           // [N] 1 / Q_jj
   float* r[2];         // only [0] is used by the two-pass iteration
@@ -309,14 +320,16 @@ __global__ void __launch_bounds__(CT) k_blk_upd(const BlkArgs* __restrict__ A, c
 // per-column partial w.u, and -- in the last CTA -- the scalar update
 // (first pass of a correction solve: alpha = gamma/delta, beta = 0;
 // afterwards the single-reduction recurrence and the stop test on r.r).
-// Each warp takes 32 consecutive rows at a time: lane l loads the neighbour
-// indices and Q_jj of row l once, then they are broadcast by shuffles.
+// A CTA takes tiles of SP_TR consecutive rows; the tile and the external rows
+// its neighbours reference are copied to shared memory first (coalesced
+// 16-byte loads, many in flight), so the gathers read shared memory; lanes
+// are columns (R = 32: one row per warp step, R < 32: 32/R rows).
 // mode: SPMM_GRAPH inside the solver graph (may end the WHILE loop),
 // SPMM_START host-launched start of a correction solve, SPMM_BENCH timing.
 constexpr int SPMM_GRAPH = 0, SPMM_BENCH = 1, SPMM_START = 2;
 
 template <int R>
-__global__ void __launch_bounds__(CT) k_blk_spmm(const BlkArgs* __restrict__ A, BlkState* st,
+__global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ A, BlkState* st,
                                                  cudaGraphConditionalHandle handle, int mode) {
   const bool bench = mode == SPMM_BENCH;
   if (mode == SPMM_GRAPH && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -335,47 +348,97 @@ __global__ void __launch_bounds__(CT) k_blk_spmm(const BlkArgs* __restrict__ A, 
   const float lam = A->lam;
   const int lane = threadIdx.x & 31, c = lane % R;
   constexpr int RPW = 32 / R;
-  const int wrp = threadIdx.x >> 5, nw = CT / 32;
+  const int wrp = threadIdx.x >> 5;
   const float* __restrict__ u = A->u;
   float* __restrict__ w = A->w[0];
   double acc = 0.0;
-  float fa = 0.0f;
-  int nchunk = 0;
-  int row0, row1;
-  cta_rows(N, &row0, &row1);
-  for (int base = row0 + 32 * wrp; base < row1; base += 32 * nw) {
-    int nbl[6] = {-1, -1, -1, -1, -1, -1};
-    float ql = 0.0f;
-    if (base + lane < row1) {
-      load_nb6(A->nb6, base + lane, nbl);
-      ql = __ldg(A->qd + base + lane);
-    }
-#pragma unroll 2
-    for (int j = 0; j < 32 / RPW; ++j) {
-      const int src = j * RPW + lane / R;
-      const int row = base + src;
-      int nb[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) nb[k] = __shfl_sync(0xffffffffu, nbl[k], src);
-      const float q = __shfl_sync(0xffffffffu, ql, src);
-      if (row >= row1) continue;
-      const size_t o = (size_t)row * R + c;
-      const float uo = u[o];
-      float un[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) un[k] = nb[k] >= 0 ? u[(size_t)nb[k] * R + c] : 0.0f;
-      const float ns = ((un[0] + un[1]) + (un[2] + un[3])) + (un[4] + un[5]);
-      const float wn = q * uo - lam * ns;
-      w[o] = wn;
-      fa += wn * uo;
-      if (++nchunk == 8) {
-        acc += (double)fa;
-        fa = 0.0f;
-        nchunk = 0;
+  // tiles of SP_TR rows: the tile's own rows and the rows outside it that its
+  // face neighbours reference (a precomputed sorted list) are copied to
+  // shared memory with coalesced 16-byte loads issued in batches, then w is
+  // formed from there.  Warp wrp owns rows [16 wrp, 16 wrp + 16) of the tile;
+  // their neighbour slots and Q_jj are fetched before the staging barrier.
+  extern __shared__ __align__(16) float us[];  // [SP_ROWS][R]
+  constexpr int Q4 = R / 4;                    // float4 per row
+  constexpr int OWN = SP_TR * Q4 / CT;         // own-row float4 per thread
+  constexpr int XN = (SP_EMAX * Q4 + CT - 1) / CT;  // external float4 per thread (at most)
+  static_assert(SP_TR * Q4 % CT == 0 && SP_TR == 16 * (CT / 32), "tile / CTA shape");
+  const float4* __restrict__ u4 = reinterpret_cast<const float4*>(u);
+  float4* us4 = reinterpret_cast<float4*>(us);
+  const int ntiles = (N + SP_TR - 1) / SP_TR;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int t0 = tile * SP_TR, t1 = min(N, t0 + SP_TR);
+    const int ne = __ldg(A->sp_ne + tile);
+    const int32_t* __restrict__ ext = A->sp_ext + (size_t)tile * SP_EMAX;
+    uint4 slv = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    float qv = 0.0f;
+    {
+      const int myrow = t0 + 16 * wrp + (lane & 15);
+      if (lane < 16 && myrow < t1) {
+        slv = __ldg(reinterpret_cast<const uint4*>(A->sp_slot) + myrow);
+        qv = __ldg(A->qd + myrow);
       }
     }
+    // issue every load whose address is known: own rows and the external
+    // row indices (the list holds SP_EMAX entries; those past ne are unused)
+    const int nown = (t1 - t0) * Q4;
+    float4 v[OWN];
+#pragma unroll
+    for (int i = 0; i < OWN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      v[i] = q < nown ? __ldg(u4 + (size_t)t0 * Q4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int ji[XN];
+#pragma unroll
+    for (int i = 0; i < XN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      ji[i] = q < SP_EMAX * Q4 ? __ldg(ext + q / Q4) : 0;
+    }
+    __syncthreads();  // the previous tile's readers are done
+#pragma unroll
+    for (int i = 0; i < OWN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      if (q < nown) us4[q] = v[i];
+    }
+    const int next = ne * Q4;
+    float4 ev[XN];
+#pragma unroll
+    for (int i = 0; i < XN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      ev[i] = q < next ? __ldg(u4 + (size_t)ji[i] * Q4 + (q % Q4)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < XN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      if (q < next) us4[SP_TR * Q4 + q] = ev[i];
+    }
+    __syncthreads();
+    float ft = 0.0f;
+#pragma unroll 4
+    for (int jstep = 0; jstep < 16 / RPW; ++jstep) {
+      const int src = jstep * RPW + lane / R;  // row of the warp's 16, and the lane holding its slots
+      const int rr = 16 * wrp + src, row = t0 + rr;
+      const uint32_t sx = __shfl_sync(0xffffffffu, slv.x, src), sy = __shfl_sync(0xffffffffu, slv.y, src),
+                     sz = __shfl_sync(0xffffffffu, slv.z, src);
+      const float q = __shfl_sync(0xffffffffu, qv, src);
+      if (row >= t1) continue;
+      const int sv[6] = {(int16_t)(sx & 0xffffu), (int16_t)(sx >> 16), (int16_t)(sy & 0xffffu),
+                         (int16_t)(sy >> 16),     (int16_t)(sz & 0xffffu), (int16_t)(sz >> 16)};
+      const float uo = us[rr * R + c];
+      float un[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const int sk = sv[k];
+        un[k] = sk < 0 ? 0.0f
+                       : (sk == SP_GLOBAL ? __ldg(u + (size_t)__ldg(A->nb6 + 6 * (size_t)row + k) * R + c)
+                                          : us[sk * R + c]);
+      }
+      const float ns = ((un[0] + un[1]) + (un[2] + un[3])) + (un[4] + un[5]);
+      const float wn = q * uo - lam * ns;
+      w[(size_t)row * R + c] = wn;
+      ft += wn * uo;
+    }
+    acc += (double)ft;  // FP32 over the tile's rows of this lane (<= 16), FP64 across tiles
   }
-  acc += (double)fa;
   double v[1] = {acc};
   column_partials<R, 1>(v, A->part);
   if (!arrive_last(&st->cnt)) return;
@@ -387,7 +450,7 @@ __global__ void __launch_bounds__(CT) k_blk_spmm(const BlkArgs* __restrict__ A, 
   __shared__ double tot1[3][MAXR];
   __shared__ int any_live;
   sum_partials<1>(A->part, R, gridDim.x, tot);
-  sum_partials<2>(A->part1, R, gridDim.x, tot1);  // pass 1: r.u, r.r
+  sum_partials<2>(A->part1, R, NCTA, tot1);  // pass 1 (NCTA CTAs): r.u, r.r
   const bool first = st->first;
   if (threadIdx.x == 0) {
     any_live = 0;
@@ -507,6 +570,94 @@ __global__ void k_nb6(BandView B, int32_t* __restrict__ nb6) {
   }
 }
 
+// SpMM plan of one tile (one CTA of 256 threads per tile): the sorted unique
+// rows outside [t0, t1) referenced by the tile's face neighbours (the first
+// SP_EMAX are staged), and per row the slot of each neighbour: own row
+// j - t0, external row SP_TR + e, -1 none, SP_GLOBAL beyond the list.
+__global__ void __launch_bounds__(256) k_sp_plan(int N, const int32_t* __restrict__ nb6, int32_t* __restrict__ ext,
+                                                 int32_t* __restrict__ ne_out, int16_t* __restrict__ slot) {
+  constexpr int C = 2048;  // >= 6 SP_TR candidates, a power of two
+  __shared__ int cand[C];
+  __shared__ int uniq[C];
+  __shared__ int cnt[256];
+  __shared__ int nc;
+  const int t0 = blockIdx.x * SP_TR, t1 = min(N, t0 + SP_TR);
+  if (threadIdx.x == 0) nc = 0;
+  for (int q = threadIdx.x; q < C; q += blockDim.x) cand[q] = INT_MAX;
+  __syncthreads();
+  for (int q = threadIdx.x; q < (t1 - t0) * 6; q += blockDim.x) {
+    const int j = nb6[6 * (size_t)t0 + q];
+    if (j >= 0 && (j < t0 || j >= t1)) cand[atomicAdd(&nc, 1)] = j;
+  }
+  __syncthreads();
+  // bitonic sort, ascending (INT_MAX padding last)
+  for (int k = 2; k <= C; k <<= 1)
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int l = threadIdx.x; l < C; l += blockDim.x) {
+        const int p = l ^ jj;
+        if (p > l) {
+          const int a = cand[l], b = cand[p];
+          if ((a > b) == ((l & k) == 0)) {
+            cand[l] = b;
+            cand[p] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  // unique: thread t keeps the first occurrences in cand[8t, 8t + 8)
+  const int base = 8 * threadIdx.x;
+  int mine = 0;
+  for (int l = base; l < base + 8; ++l)
+    mine += cand[l] != INT_MAX && (l == 0 || cand[l] != cand[l - 1]);
+  cnt[threadIdx.x] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const int c = cnt[t];
+      cnt[t] = run;
+      run += c;
+    }
+    nc = run;
+  }
+  __syncthreads();
+  int pos = cnt[threadIdx.x];
+  for (int l = base; l < base + 8; ++l)
+    if (cand[l] != INT_MAX && (l == 0 || cand[l] != cand[l - 1])) uniq[pos++] = cand[l];
+  __syncthreads();
+  const int ne = nc, nkeep = min(ne, SP_EMAX);
+  for (int e = threadIdx.x; e < nkeep; e += blockDim.x) ext[(size_t)blockIdx.x * SP_EMAX + e] = uniq[e];
+  if (threadIdx.x == 0) ne_out[blockIdx.x] = nkeep;
+  for (int row = t0 + threadIdx.x; row < t1; row += blockDim.x) {
+    int16_t sv[8];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int j = nb6[6 * (size_t)row + k];
+      int16_t v = -1;
+      if (j >= t0 && j < t1) {
+        v = (int16_t)(j - t0);
+      } else if (j >= 0) {
+        int lo = 0, hi = ne;  // first index with uniq[idx] >= j
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (uniq[mid] < j) lo = mid + 1;
+          else hi = mid;
+        }
+        v = lo < SP_EMAX ? (int16_t)(SP_TR + lo) : SP_GLOBAL;
+      }
+      sv[k] = v;
+    }
+    sv[6] = sv[7] = -1;
+    uint4 o;
+    o.x = (uint16_t)sv[0] | ((uint32_t)(uint16_t)sv[1] << 16);
+    o.y = (uint16_t)sv[2] | ((uint32_t)(uint16_t)sv[3] << 16);
+    o.z = (uint16_t)sv[4] | ((uint32_t)(uint16_t)sv[5] << 16);
+    o.w = (uint16_t)sv[6] | ((uint32_t)(uint16_t)sv[7] << 16);
+    reinterpret_cast<uint4*>(slot)[row] = o;
+  }
+}
+
 __global__ void k_inv(int N, const float* __restrict__ qd, float* __restrict__ iq) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) iq[i] = 1.0f / qd[i];
 }
@@ -551,6 +702,8 @@ __global__ void k_bench_state(BlkState* st) {
     st->all_done = 0;
   }
 }
+
+constexpr size_t sp_smem(int R) { return (size_t)SP_ROWS * R * sizeof(float); }
 
 unsigned grid_for(int64_t n, int threads, int64_t cap) {
   int64_t g = (n + threads - 1) / threads;
@@ -599,7 +752,7 @@ void block_graph_free(BlockGraph* g) {
 template <int R>
 static void blk_iter(BlockGraph* g, cudaStream_t s, cudaGraphConditionalHandle h, int bench = 0) {
   k_blk_upd<R, false><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
-  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, h, bench ? SPMM_BENCH : SPMM_GRAPH);
+  k_blk_spmm<R><<<SP_NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, h, bench ? SPMM_BENCH : SPMM_GRAPH);
 }
 
 // start of a correction solve from r: u, p = s = x = 0, w = Q u, alpha
@@ -607,7 +760,7 @@ template <int R>
 static void blk_start(BlockGraph* g, cudaStream_t s) {
   k_blk_upd<R, true><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
   count_launch();
-  k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_START);
+  k_blk_spmm<R><<<SP_NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_START);
   count_launch();
 }
 
@@ -629,6 +782,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
   if (!g) {
     g = new BlockGraph();
     g->R = R;
+    BF_CK(cudaFuncSetAttribute(k_blk_spmm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
     memset(&g->h, 0, sizeof(g->h));
     BF_CK(cudaMalloc(&g->d_args, sizeof(BlkArgs)));
     BF_CK(cudaMallocHost(&g->h_pin, sizeof(BlkArgs)));
@@ -668,7 +822,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     BF_CK(cudaMalloc(&g->Z, nv * 2));
     BF_CK(cudaMalloc(&g->h.iq, (size_t)rows * 4));
     BF_CK(cudaMalloc(&g->sacc, (size_t)rows * 8));
-    BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NCTA * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NPART * sizeof(double)));
     BF_CK(cudaMalloc(&g->h.part1, (size_t)2 * R * NCTA * sizeof(double)));
     g->cap_rows = rows;
   }
@@ -677,9 +831,22 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     k_nb6<<<grid_for(b->N, 256, 152 * 16), 256, 0, s>>>(band_view(b), b->nb6);
     count_launch();
   }
+  if (!b->sp_slot) {
+    const int nt = (int)((b->N + SP_TR - 1) / SP_TR);
+    BF_TRY(dev_alloc_t(ctx, &b->sp_ext, (size_t)SP_EMAX * (nt ? nt : 1)));
+    BF_TRY(dev_alloc_t(ctx, &b->sp_ne, (size_t)(nt ? nt : 1)));
+    BF_TRY(dev_alloc_t(ctx, &b->sp_slot, (size_t)8 * (b->N ? b->N : 1)));
+    if (nt) {
+      k_sp_plan<<<nt, 256, 0, s>>>((int)b->N, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot);
+      count_launch();
+    }
+  }
   g->h.N = (int)b->N;
   g->h.lam = (float)b->prm.lambda;
   g->h.nb6 = b->nb6;
+  g->h.sp_ext = b->sp_ext;
+  g->h.sp_ne = b->sp_ne;
+  g->h.sp_slot = b->sp_slot;
   g->h.qd = b->qd;
   g->h.Z = g->Z;
   // the previous upload from h_pin has completed: every solve ends with a sync
@@ -772,7 +939,7 @@ static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int which, int reps, doubl
       count_launch();
     }
     if (which != 1) {
-      k_blk_spmm<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_BENCH);
+      k_blk_spmm<R><<<SP_NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_BENCH);
       count_launch();
     }
   }

@@ -82,6 +82,9 @@ struct bf_band {
   float* rhs = nullptr;       // [N] h_j
   bool integrated = false;
   int32_t* nb6 = nullptr;     // [N][6] face-neighbour indices (probe solver)
+  int32_t* sp_ext = nullptr;  // probe-solver SpMM plan: external rows per tile
+  int32_t* sp_ne = nullptr;   //   their count per tile
+  int16_t* sp_slot = nullptr; //   [N][8] staged-row slot of each face neighbour
 };
 
 // POD view of a band passed to kernels.

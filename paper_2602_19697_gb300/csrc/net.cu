@@ -589,6 +589,43 @@ static bf_status net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, const f
   return BF_OK;
 }
 
+// gradient of the loss of the last net_forward with targets, into net->g
+static bf_status net_backward(bf_ctx* ctx, bf_net* net, const bf_band* b) {
+  cudaStream_t s = ctx->stream;
+  const int nb = b->NB;
+  const int grid = nb < 152 ? nb : 152;
+  for (int l = 0; l < 4; ++l) BF_CK(cudaMemsetAsync(net->gpad[l], 0, (size_t)27 * CI_PAD[l] * CO_PAD[l] * 4, s));
+  BF_CK(cudaMemsetAsync(net->g, 0, net->P * 4, s));
+  LossArgs none;
+  memset(&none, 0, sizeof(none));
+  // layer 4 (dy = act[4], written by the forward pass)
+  k_wgrad<32, 16><<<grid, NT, wgrad_smem<32, 16>(), s>>>(nb, net->act[3], net->act[4], net->gpad[3],
+                                                         net->g + net->boff[3], CO_REAL[3]);
+  k_conv<16, 32, MODE_DGRAD><<<grid, NT, conv_smem<16, 32>(), s>>>(nb, net->act[4], net->wb[3], nullptr, 0,
+                                                                   net->gact[2], net->act[3], none);
+  // layer 3
+  k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[2], net->gact[2], net->gpad[2],
+                                                         net->g + net->boff[2], CO_REAL[2]);
+  k_conv<32, 32, MODE_DGRAD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->gact[2], net->wb[2], nullptr, 0,
+                                                                   net->gact[1], net->act[2], none);
+  // layer 2
+  k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->gact[1], net->gpad[1],
+                                                         net->g + net->boff[1], CO_REAL[1]);
+  k_conv<32, 32, MODE_DGRAD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->gact[1], net->wb[1], nullptr, 0,
+                                                                   net->gact[0], net->act[1], none);
+  // layer 1
+  k_wgrad<16, 32><<<grid, NT, wgrad_smem<16, 32>(), s>>>(nb, net->act[0], net->gact[0], net->gpad[0],
+                                                         net->g + net->boff[0], CO_REAL[0]);
+  count_launch(7);
+  for (int l = 0; l < 4; ++l) {
+    k_unpad_grad<<<gs(27 * CI_REAL[l] * CO_REAL[l]), 256, 0, s>>>(net->gpad[l], CI_REAL[l], CO_REAL[l], CI_PAD[l],
+                                                                 CO_PAD[l], net->g + net->woff[l]);
+    count_launch();
+  }
+  BF_CK(cudaGetLastError());
+  return BF_OK;
+}
+
 extern "C" {
 
 int64_t bf_net_nparams(void) { return nparams_impl(); }
@@ -694,43 +731,14 @@ bf_status bf_net_train_step(bf_ctx* ctx, bf_net* net, const bf_band* b, const fl
   const float *dmu, *dst;
   BF_TRY(stage_in(ctx, mu_t, b->N, WS_STAGE2, &dmu));
   BF_TRY(stage_in(ctx, s_t, b->N, WS_STAGE3, &dst));
-  const int nb = b->NB;
-  const int grid = nb < 152 ? nb : 152;
   BF_TRY(net_forward(ctx, net, b, dmu, dst, nullptr, nullptr));
-  for (int l = 0; l < 4; ++l) BF_CK(cudaMemsetAsync(net->gpad[l], 0, (size_t)27 * CI_PAD[l] * CO_PAD[l] * 4, s));
-  BF_CK(cudaMemsetAsync(net->g, 0, net->P * 4, s));
-  LossArgs none;
-  memset(&none, 0, sizeof(none));
-  // layer 4 (dy = act[4], written by the forward pass)
-  k_wgrad<32, 16><<<grid, NT, wgrad_smem<32, 16>(), s>>>(nb, net->act[3], net->act[4], net->gpad[3],
-                                                         net->g + net->boff[3], CO_REAL[3]);
-  k_conv<16, 32, MODE_DGRAD><<<grid, NT, conv_smem<16, 32>(), s>>>(nb, net->act[4], net->wb[3], nullptr, 0,
-                                                                   net->gact[2], net->act[3], none);
-  // layer 3
-  k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[2], net->gact[2], net->gpad[2],
-                                                         net->g + net->boff[2], CO_REAL[2]);
-  k_conv<32, 32, MODE_DGRAD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->gact[2], net->wb[2], nullptr, 0,
-                                                                   net->gact[1], net->act[2], none);
-  // layer 2
-  k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->gact[1], net->gpad[1],
-                                                         net->g + net->boff[1], CO_REAL[1]);
-  k_conv<32, 32, MODE_DGRAD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->gact[1], net->wb[1], nullptr, 0,
-                                                                   net->gact[0], net->act[1], none);
-  // layer 1
-  k_wgrad<16, 32><<<grid, NT, wgrad_smem<16, 32>(), s>>>(nb, net->act[0], net->gact[0], net->gpad[0],
-                                                         net->g + net->boff[0], CO_REAL[0]);
-  count_launch(7);
-  for (int l = 0; l < 4; ++l) {
-    k_unpad_grad<<<gs(27 * CI_REAL[l] * CO_REAL[l]), 256, 0, s>>>(net->gpad[l], CI_REAL[l], CO_REAL[l], CI_PAD[l],
-                                                                 CO_PAD[l], net->g + net->woff[l]);
-    count_launch();
-  }
+  BF_TRY(net_backward(ctx, net, b));
   BF_CK(cudaGetLastError());
   if (grad_out) BF_CK(cudaMemcpyAsync(grad_out, net->g, net->P * 4, cudaMemcpyDefault, s));
-  net->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.0f - powf(b1, (float)net->step), c2 = 1.0f - powf(b2, (float)net->step);
   if (lr > 0.0f) {
+    net->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - powf(b1, (float)net->step), c2 = 1.0f - powf(b2, (float)net->step);
     k_adam<<<gs(net->P), 256, 0, s>>>((int)net->P, net->p, net->g, net->m, net->v, lr, b1, b2, c1, c2, 1e-8f);
     count_launch();
     BF_TRY(net_pack(ctx, net));
@@ -809,6 +817,49 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
   if (n_accepted) *n_accepted = h_nacc;
   if (total_iters) *total_iters = it_j + it_r;
   return done(BF_OK);
+}
+
+bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* b, int which, int reps, double* ms) {
+  if (!ctx || !net || !b || !ms || reps < 1 || which < 0 || which > 3) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_net_bench: call bf_integrate_depth first");
+  *ms = 0.0;
+  if (b->NB == 0) return BF_OK;
+  cudaStream_t s = ctx->stream;
+  const int nb = b->NB;
+  const int grid = nb < 152 ? nb : 152;
+  // one forward with (arbitrary, finite) targets so that every buffer holds data
+  BF_TRY(net_forward(ctx, net, b, b->tsdf, b->d, nullptr, nullptr));
+  LossArgs none;
+  memset(&none, 0, sizeof(none));
+  cudaEvent_t e0, e1;
+  BF_CK(cudaEventCreate(&e0));
+  BF_CK(cudaEventCreate(&e1));
+  BF_CK(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i) {
+    if (which == BF_NET_BENCH_FORWARD) {
+      BF_TRY(net_forward(ctx, net, b, nullptr, nullptr, nullptr, nullptr));
+    } else if (which == BF_NET_BENCH_TRAIN) {
+      BF_TRY(net_forward(ctx, net, b, b->tsdf, b->d, nullptr, nullptr));
+      BF_TRY(net_backward(ctx, net, b));
+    } else if (which == BF_NET_BENCH_CONV) {
+      k_conv<32, 32, MODE_FWD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->act[1], net->wf[1],
+                                                                     net->p + net->boff[1], CO_REAL[1], net->act[2],
+                                                                     nullptr, none);
+      count_launch();
+    } else {
+      k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->act[2], net->gpad[1],
+                                                             net->g + net->boff[1], CO_REAL[1]);
+      count_launch();
+    }
+  }
+  BF_CK(cudaEventRecord(e1, s));
+  BF_CK(cudaEventSynchronize(e1));
+  float t = 0.0f;
+  BF_CK(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  return BF_OK;
 }
 
 }  // extern "C"

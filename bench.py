@@ -279,26 +279,21 @@ def run_ours(args, world, rank, local):
     band.integrate_depth(depth, poses, w.intr)
     s = torch.empty(band.N, device=dev)
     band.estimate_variance(s, K=R, seed=0, rel_tol=args.tol, rhs_block=R)
-    ms_upd = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_UPDATE, R=R, reps=50)
-    ms_spmm = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_SPMM, R=R, reps=50)
     ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R, reps=50)
     N, NB = band.N, band.NB
-    # algorithmic bytes of the probe solver's passes (per voxel row of R columns):
-    # update pass: r, w, s, p, x read, p, s, x, r, u written (40 B per column),
-    # 1/Q_jj read (4 B); SpMM pass: u read, w written (8 B per column), six
-    # neighbour indices and Q_jj read (28 B)
-    bytes_upd = N * (R * 40 + 4)
-    bytes_spmm = N * (R * 8 + 28)
+    # algorithmic bytes of one probe-solver iteration (per voxel row of R
+    # columns): r, w, s, p, x read and p, x, r', s', w' written (40 B per
+    # column), Q_jj and 1/Q_jj read (8 B); the neighbour gathers of the SpMM
+    # are not counted (they come from shared memory and L2 by design)
+    bytes_it = N * (R * 40 + 8)
     ms_spmv = band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=200)
     bytes_spmv = N * 12 + NB * (128 + 24)   # x, qd read, y written; brick metadata
-    achieved = bytes_upd / (ms_upd * 1e-3) / 1e9
-    roof = {"kernel": "k_blk_upd<%d> (probe-solver vector-update pass, the dominant kernel)" % R, "bound": "hbm",
+    achieved = bytes_it / (ms_iter * 1e-3) / 1e9
+    roof = {"kernel": "k_blk_it<%d> (one probe-solver iteration: vector updates and w = Q u in one pass, "
+                      "the dominant kernel)" % R, "bound": "hbm",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-            "peak_kind": peak_kind, "traffic": None, "bytes_per_launch": bytes_upd,
-            "ms_per_launch": round(ms_upd, 5),
-            "spmm_pass": {"kernel": "k_blk_spmm<%d>" % R, "ms_per_launch": round(ms_spmm, 5),
-                          "achieved": round(bytes_spmm / (ms_spmm * 1e-3) / 1e9, 1), "bytes_per_launch": bytes_spmm},
-            "iteration": {"ms": round(ms_iter, 5), "achieved": round((bytes_upd + bytes_spmm) / (ms_iter * 1e-3) / 1e9, 1)}}
+            "peak_kind": peak_kind, "traffic": None, "bytes_per_launch": bytes_it,
+            "ms_per_launch": round(ms_iter, 5)}
     spmv = {"kernel": "k_brick (7-point SpMV, single RHS)", "achieved": round(bytes_spmv / (ms_spmv * 1e-3) / 1e9, 1),
             "ms_per_launch": round(ms_spmv, 5), "bytes_per_launch": bytes_spmv,
             "note": "single-RHS vectors of this workload are L2-resident (%.1f MB)" % (N * 12 / 1e6)}

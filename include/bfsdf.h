@@ -301,14 +301,10 @@ bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* band, int which,
  * and returns the mean time per repetition (ms).
  *   BF_KERNEL_SPMV: the 7-point SpMV y = Q x over the band (bf_spmv's kernel);
  *   BF_KERNEL_BLOCK_ITER: one probe-solver iteration over R = 8, 16 or 32
- *     columns (BF_KERNEL_BLOCK_UPDATE followed by BF_KERNEL_BLOCK_SPMM);
- *   BF_KERNEL_BLOCK_UPDATE: its streaming vector-update pass;
- *   BF_KERNEL_BLOCK_SPMM: its w = Q u pass.
+ *     columns (the single-pass kernel: vector updates and w = Q u).
  * Inputs are the library's own workspaces (their values are not preserved). */
 #define BF_KERNEL_SPMV 0
 #define BF_KERNEL_BLOCK_ITER 1
-#define BF_KERNEL_BLOCK_UPDATE 2
-#define BF_KERNEL_BLOCK_SPMM 3
 bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* band, int which, int R, int reps, double* ms_per_launch);
 
 /* Number of GPU kernels this library has run in this process (host launches

@@ -403,9 +403,7 @@ bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, d
     *ms_per_launch = t / reps;
     return BF_OK;
   }
-  if (which == BF_KERNEL_BLOCK_ITER) return bench_block_spmv(ctx, b, 0, R, reps, ms_per_launch);
-  if (which == BF_KERNEL_BLOCK_UPDATE) return bench_block_spmv(ctx, b, 1, R, reps, ms_per_launch);
-  if (which == BF_KERNEL_BLOCK_SPMM) return bench_block_spmv(ctx, b, 2, R, reps, ms_per_launch);
+  if (which == BF_KERNEL_BLOCK_ITER) return bench_block_iter(ctx, b, R, reps, ms_per_launch);
   return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: unknown kernel");
 }
 

@@ -11,16 +11,15 @@
 //   p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
 //   u = r / qd,      w = Q u,        gamma = r.u,   delta = w.u,  r.r
 // with s = Q p carried by recurrence, so Q is applied once per iteration, to
-// u.  Two passes per iteration:
-//   k_blk_upd   streaming, float4 over 4 columns, in place: p, s, x, r, u and
-//               the partial sums of r.u and r.r (no neighbour access);
-//   k_blk_spmm  w = Q u: a warp takes 32/R rows at a time (lane = column),
-//               reading u at the six neighbours through a per-voxel
-//               neighbour table that each warp loads for 32 rows at once and
-//               broadcasts by shuffles; partial sums of w.u.
-// Partial sums are FP32 products summed over chunks of 8, accumulated in
-// FP64, reduced per CTA and then by the last CTA in a fixed order
-// (deterministic), which updates per column
+// u, and u = r / qd is never stored.  One pass per iteration (k_blk_it) over
+// tiles of consecutive rows: the own rows' vectors are updated (streaming,
+// float4 over 4 columns), u' of the own rows and of the rows outside the tile
+// that its face neighbours reference (a per-band gather plan) goes to shared
+// memory, and w' = Q u' is formed from there.  r, w, s are double-buffered,
+// since other CTAs recompute u' of a row from its old r, w, s.
+// Partial sums are FP32 products summed per thread, accumulated in FP64 from
+// the CTA reduction on, reduced per CTA and then by the last CTA in a fixed
+// order (deterministic), which updates per column
 //   beta' = gamma'/gamma,  alpha' = gamma' / (delta' - beta' gamma'/alpha)
 // and the stop flags.  The iteration loop is a CUDA-graph WHILE node.
 //
@@ -51,8 +50,7 @@ constexpr int NCTA = 152 * 2;
 // memory (a tile whose external rows overflow the list)
 constexpr int SP_TR = 256, SP_EMAX = 384, SP_ROWS = SP_TR + SP_EMAX;
 constexpr int16_t SP_GLOBAL = 32767;
-constexpr int SP_NCTA = 152 * 2;
-constexpr int NPART = SP_NCTA > NCTA ? SP_NCTA : NCTA;
+
 
 struct BlkState {
   double alpha[MAXR], beta[MAXR], gamma[MAXR], rr[MAXR], bb[MAXR], tol2[MAXR];
@@ -60,7 +58,8 @@ struct BlkState {
   int done[MAXR], iters[MAXR];
   double tol0;
   int iter, max_iter, all_done, status, ncols;
-  int first;  // the next pass-2 finalize starts a correction solve
+  int first;  // the next finalize starts a correction solve
+  int par;    // which of the double-buffered r, w, s is current
   unsigned int cnt, guard;
   unsigned int nexec;  // graph-body kernels executed (for launch accounting)
 };
@@ -75,12 +74,11 @@ struct BlkArgs {
   const int16_t* sp_slot;  // [N][8] staged slot of each face neighbour (6 used)
   const float* qd;     // [N] Q_jj
   float* iq;           // [N] 1 / Q_jj
-  float* r[2];         // only [0] is used by the two-pass iteration
-  float* w[2];
-  float* s[2];
+  float* r[2];         // residual, double-buffered ([BlkState::par] is current)
+  float* w[2];         // Q u
+  float* s[2];         // Q p (by recurrence)
   float* p;
   float* x;            // FP32 correction
-  float* u;            // M^-1 r
   double* x64;         // FP64 master iterates
   const __nv_bfloat16* Z;
   double* part;        // [3][R][NCTA]
@@ -162,7 +160,7 @@ __device__ __forceinline__ void load_nb6(const int32_t* __restrict__ nb6, int ro
 }
 
 // True residual of the FP64 master iterates, per column: r = z - Q x64 with
-// FP64 arithmetic, stored as the FP32 right-hand side (r[0]) of the next
+// FP64 arithmetic, stored as the FP32 right-hand side (r[par]) of the next
 // correction solve; per-column r.r and z.z.  The last CTA sets, per column,
 // the stop flag (true residual within tolerance) and the correction target
 // eta = 0.5 tol |z| / |r| clamped to [1e-5, 0.5].
@@ -187,7 +185,7 @@ __global__ void __launch_bounds__(CT) k_blk_outer(const BlkArgs* __restrict__ A,
       if (nb[k] >= 0) ns += x64[(size_t)nb[k] * R + c];
     const double z = (double)__bfloat162float(A->Z[o]);
     const double r = z - ((double)__ldg(A->qd + row) * x64[o] - (double)lam * ns);
-    A->r[0][o] = (float)r;
+    A->r[st->par][o] = (float)r;
     acc[0] += r * r;
     acc[1] += z * z;
   }
@@ -220,120 +218,49 @@ __global__ void __launch_bounds__(CT) k_blk_outer(const BlkArgs* __restrict__ A,
   }
 }
 
-// Pass 1 of an iteration (streaming, float4 over 4 columns of a row, in
-// place): with u = r/qd,
-//   INIT:   u;                     x = p = s = 0
-//   normal: p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s,
-//           u = r/qd
-// and the per-column partial sums gamma = r.u, r.r -> part[0..1].
-template <int R, bool INIT>
-__global__ void __launch_bounds__(CT) k_blk_upd(const BlkArgs* __restrict__ A, const BlkState* __restrict__ st) {
-  if (!INIT && st->all_done) return;
-  constexpr int G = R / 4;
-  const int N = A->N;
-  const int g = threadIdx.x % G;  // column group of this thread (fixed: the stride is a multiple of G)
-  float4 al = make_float4(0.f, 0.f, 0.f, 0.f), be = al;
-  if (!INIT) {
-    al = make_float4((float)st->alpha[4 * g], (float)st->alpha[4 * g + 1], (float)st->alpha[4 * g + 2],
-                     (float)st->alpha[4 * g + 3]);
-    be = make_float4((float)st->beta[4 * g], (float)st->beta[4 * g + 1], (float)st->beta[4 * g + 2],
-                     (float)st->beta[4 * g + 3]);
-  }
-  float4* __restrict__ r = (float4*)A->r[0];
-  float4* __restrict__ w = (float4*)A->w[0];
-  float4* __restrict__ sv = (float4*)A->s[0];
-  float4* __restrict__ p = (float4*)A->p;
-  float4* __restrict__ x = (float4*)A->x;
-  float4* __restrict__ u = (float4*)A->u;
-  const float* __restrict__ iq = A->iq;
-  double acc[8];
-  float fa[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    acc[k] = 0.0;
-    fa[k] = 0.0f;
-  }
-  int nchunk = 0;
-  const int64_t n4 = (int64_t)N * G;
-  for (int64_t e = (int64_t)blockIdx.x * CT + threadIdx.x; e < n4; e += (int64_t)gridDim.x * CT) {
-    const float q = iq[e / G];
-    float4 ri = r[e], un;
-    if (INIT) {
-      un = make_float4(ri.x * q, ri.y * q, ri.z * q, ri.w * q);
-      const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-      x[e] = z;
-      p[e] = z;
-      sv[e] = z;
-    } else {
-      const float4 wi = w[e], si = sv[e], pi = p[e], xi = x[e];
-      // beta = 0 starts a new direction: do not touch the previous p, s
-      float4 pn, sn;
-      pn.x = ri.x * q + (be.x != 0.f ? be.x * pi.x : 0.f);
-      pn.y = ri.y * q + (be.y != 0.f ? be.y * pi.y : 0.f);
-      pn.z = ri.z * q + (be.z != 0.f ? be.z * pi.z : 0.f);
-      pn.w = ri.w * q + (be.w != 0.f ? be.w * pi.w : 0.f);
-      sn.x = wi.x + (be.x != 0.f ? be.x * si.x : 0.f);
-      sn.y = wi.y + (be.y != 0.f ? be.y * si.y : 0.f);
-      sn.z = wi.z + (be.z != 0.f ? be.z * si.z : 0.f);
-      sn.w = wi.w + (be.w != 0.f ? be.w * si.w : 0.f);
-      x[e] = make_float4(xi.x + al.x * pn.x, xi.y + al.y * pn.y, xi.z + al.z * pn.z, xi.w + al.w * pn.w);
-      ri = make_float4(ri.x - al.x * sn.x, ri.y - al.y * sn.y, ri.z - al.z * sn.z, ri.w - al.w * sn.w);
-      un = make_float4(ri.x * q, ri.y * q, ri.z * q, ri.w * q);
-      p[e] = pn;
-      sv[e] = sn;
-      r[e] = ri;
-    }
-    u[e] = un;
-    fa[0] += ri.x * un.x; fa[1] += ri.y * un.y; fa[2] += ri.z * un.z; fa[3] += ri.w * un.w;
-    fa[4] += ri.x * ri.x; fa[5] += ri.y * ri.y; fa[6] += ri.z * ri.z; fa[7] += ri.w * ri.w;
-    if (++nchunk == 8) {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        acc[k] += (double)fa[k];
-        fa[k] = 0.0f;
-      }
-      nchunk = 0;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 8; ++k) acc[k] += (double)fa[k];
-  // per-column CTA sums: lanes sharing threadIdx % G, then warps
-  __shared__ double sh[CT / 32][8][8];
-  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    for (int o = 16; o >= G; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-  if (lane < G) {
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sh[wrp][lane][k] = acc[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < 2 * R) {
-    const int q = threadIdx.x / R, c = threadIdx.x % R;  // q: 0 = r.u, 1 = r.r
-    double t = 0.0;
-    for (int ww = 0; ww < CT / 32; ++ww) t += sh[ww][c / 4][4 * q + (c & 3)];
-    A->part1[((size_t)q * R + c) * gridDim.x + blockIdx.x] = t;
-  }
+// Element update of one row, float4 over 4 columns (separately rounded, so
+// that a row's u comes out bit-identical in the CTA that owns the row and in
+// every CTA that stages it as an external neighbour):
+//   s' = w + beta s,  r' = r - alpha s',  u' = r' / Q_jj
+// (beta == 0 starts a new direction: the old s is not read).
+__device__ __forceinline__ float bmul(float b, float v) { return b != 0.f ? __fmul_rn(b, v) : 0.f; }
+__device__ __forceinline__ float4 next_s(float4 w, float4 s, float4 be) {
+  return make_float4(__fadd_rn(w.x, bmul(be.x, s.x)), __fadd_rn(w.y, bmul(be.y, s.y)), __fadd_rn(w.z, bmul(be.z, s.z)),
+                     __fadd_rn(w.w, bmul(be.w, s.w)));
+}
+__device__ __forceinline__ float4 next_r(float4 r, float4 sn, float4 al) {
+  return make_float4(__fsub_rn(r.x, __fmul_rn(al.x, sn.x)), __fsub_rn(r.y, __fmul_rn(al.y, sn.y)),
+                     __fsub_rn(r.z, __fmul_rn(al.z, sn.z)), __fsub_rn(r.w, __fmul_rn(al.w, sn.w)));
+}
+__device__ __forceinline__ float4 scale4(float4 a, float q) {
+  return make_float4(__fmul_rn(a.x, q), __fmul_rn(a.y, q), __fmul_rn(a.z, q), __fmul_rn(a.w, q));
 }
 
-// Pass 2: w = Q u (7-point, u gathered from the six neighbour rows), the
-// per-column partial w.u, and -- in the last CTA -- the scalar update
-// (first pass of a correction solve: alpha = gamma/delta, beta = 0;
-// afterwards the single-reduction recurrence and the stop test on r.r).
-// A CTA takes tiles of SP_TR consecutive rows; the tile and the external rows
-// its neighbours reference are copied to shared memory first (coalesced
-// 16-byte loads, many in flight), so the gathers read shared memory; lanes
-// are columns (R = 32: one row per warp step, R < 32: 32/R rows).
-// mode: SPMM_GRAPH inside the solver graph (may end the WHILE loop),
-// SPMM_START host-launched start of a correction solve, SPMM_BENCH timing.
-constexpr int SPMM_GRAPH = 0, SPMM_BENCH = 1, SPMM_START = 2;
+// One block-PCG iteration in one pass over the band (mode as below):
+//   phase 1, the tile's own rows (float4 over 4 columns, streaming):
+//     u = r/Q_jj, p = u + beta p, s' = w + beta s, x += alpha p,
+//     r' = r - alpha s', u' = r'/Q_jj; partial sums r'.u', r'.r'
+//   phase 2, the external rows its face neighbours reference: u' from their
+//     (old) r, w, s by the same arithmetic
+//   phase 3, w' = Q u' for the own rows from the staged u'; partial w'.u'.
+// INIT (start of a correction solve from r): u = r/Q_jj, p = u, x = s' = 0,
+// r' = r, w' = Q u.  r, w, s are double-buffered (read [par], written
+// [par ^ 1]; other CTAs read the old values of rows this CTA updates); p and
+// x are updated in place.  The last CTA reduces the partial sums in a fixed
+// order and updates the per-column scalars (first pass of a correction
+// solve: alpha = gamma/delta, beta = 0; afterwards the single-reduction
+// recurrence and the stop test on r.r), then flips par.
+// mode: IT_GRAPH inside the solver graph (may end the WHILE loop), IT_START
+// host-launched start of a correction solve, IT_BENCH timing (scalars, par
+// and data are left as they are: alpha = beta = 0 keeps the data fixed).
+constexpr int IT_GRAPH = 0, IT_BENCH = 1, IT_START = 2;
 
-template <int R>
-__global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ A, BlkState* st,
-                                                 cudaGraphConditionalHandle handle, int mode) {
-  const bool bench = mode == SPMM_BENCH;
-  if (mode == SPMM_GRAPH && blockIdx.x == 0 && threadIdx.x == 0) {
-    st->nexec += 2;  // this kernel and the update pass before it
+template <int R, bool INIT>
+__global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A, BlkState* st,
+                                                  cudaGraphConditionalHandle handle, int mode) {
+  const bool bench = mode == IT_BENCH;
+  if (mode == IT_GRAPH && blockIdx.x == 0 && threadIdx.x == 0) {
+    st->nexec += 1;
     unsigned gd = atomicAdd(&st->guard, 1u);
     if (st->all_done || gd > 2u * (unsigned)st->max_iter + 64u) {
       if (!st->all_done) {
@@ -343,27 +270,41 @@ __global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ 
       cudaGraphSetConditional(handle, 0);
     }
   }
-  if (!bench && st->all_done) return;
+  if (!INIT && !bench && st->all_done) return;
+  constexpr int Q4 = R / 4;                          // float4 per row
+  constexpr int OWN = SP_TR * Q4 / CT;               // own-row float4 per thread
+  constexpr int XN = (SP_EMAX * Q4 + CT - 1) / CT;  // external float4 per thread (at most)
+  constexpr int RPW = 32 / R;
+  static_assert(SP_TR * Q4 % CT == 0 && SP_TR == 16 * (CT / 32), "tile / CTA shape");
   const int N = A->N;
   const float lam = A->lam;
-  const int lane = threadIdx.x & 31, c = lane % R;
-  constexpr int RPW = 32 / R;
-  const int wrp = threadIdx.x >> 5;
-  const float* __restrict__ u = A->u;
-  float* __restrict__ w = A->w[0];
-  double acc = 0.0;
-  // tiles of SP_TR rows: the tile's own rows and the rows outside it that its
-  // face neighbours reference (a precomputed sorted list) are copied to
-  // shared memory with coalesced 16-byte loads issued in batches, then w is
-  // formed from there.  Warp wrp owns rows [16 wrp, 16 wrp + 16) of the tile;
-  // their neighbour slots and Q_jj are fetched before the staging barrier.
-  extern __shared__ __align__(16) float us[];  // [SP_ROWS][R]
-  constexpr int Q4 = R / 4;                    // float4 per row
-  constexpr int OWN = SP_TR * Q4 / CT;         // own-row float4 per thread
-  constexpr int XN = (SP_EMAX * Q4 + CT - 1) / CT;  // external float4 per thread (at most)
-  static_assert(SP_TR * Q4 % CT == 0 && SP_TR == 16 * (CT / 32), "tile / CTA shape");
-  const float4* __restrict__ u4 = reinterpret_cast<const float4*>(u);
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5, c = lane % R;
+  const int par = bench ? 0 : st->par;
+  const float4* __restrict__ rA = reinterpret_cast<const float4*>(A->r[par]);
+  const float4* __restrict__ wA = reinterpret_cast<const float4*>(A->w[par]);
+  const float4* __restrict__ sA = reinterpret_cast<const float4*>(A->s[par]);
+  float4* __restrict__ rB = reinterpret_cast<float4*>(A->r[par ^ 1]);
+  float4* __restrict__ sB = reinterpret_cast<float4*>(A->s[par ^ 1]);
+  float* __restrict__ wB = A->w[par ^ 1];
+  float4* __restrict__ p4 = reinterpret_cast<float4*>(A->p);
+  float4* __restrict__ x4 = reinterpret_cast<float4*>(A->x);
+  const float* __restrict__ iq = A->iq;
+  // this thread's 4 columns in phases 1 and 2 (the float4 index stride CT is a multiple of Q4)
+  const int g = threadIdx.x % Q4;
+  float4 al = make_float4(0.f, 0.f, 0.f, 0.f), be = al;
+  if (!INIT && !bench) {
+    al = make_float4((float)st->alpha[4 * g], (float)st->alpha[4 * g + 1], (float)st->alpha[4 * g + 2],
+                     (float)st->alpha[4 * g + 3]);
+    be = make_float4((float)st->beta[4 * g], (float)st->beta[4 * g + 1], (float)st->beta[4 * g + 2],
+                     (float)st->beta[4 * g + 3]);
+  }
+  extern __shared__ __align__(16) float us[];  // [SP_ROWS][R] u' of the own and external rows
   float4* us4 = reinterpret_cast<float4*>(us);
+  // per-thread FP32 partial sums over the CTA's tiles (at most 4 products per
+  // tile and thread), FP64 from the CTA reduction on
+  float fa[8], ft = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) fa[k] = 0.0f;
   const int ntiles = (N + SP_TR - 1) / SP_TR;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int t0 = tile * SP_TR, t1 = min(N, t0 + SP_TR);
@@ -378,41 +319,66 @@ __global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ 
         qv = __ldg(A->qd + myrow);
       }
     }
-    // issue every load whose address is known: own rows and the external
-    // row indices (the list holds SP_EMAX entries; those past ne are unused)
-    const int nown = (t1 - t0) * Q4;
-    float4 v[OWN];
-#pragma unroll
-    for (int i = 0; i < OWN; ++i) {
-      const int q = threadIdx.x + i * CT;
-      v[i] = q < nown ? __ldg(u4 + (size_t)t0 * Q4 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
     int ji[XN];
 #pragma unroll
     for (int i = 0; i < XN; ++i) {
       const int q = threadIdx.x + i * CT;
       ji[i] = q < SP_EMAX * Q4 ? __ldg(ext + q / Q4) : 0;
     }
-    __syncthreads();  // the previous tile's readers are done
-#pragma unroll
+    __syncthreads();  // the previous tile's readers of us are done
+    // phase 1: own rows
+    const int nown = (t1 - t0) * Q4;
+#pragma unroll 1
     for (int i = 0; i < OWN; ++i) {
       const int q = threadIdx.x + i * CT;
-      if (q < nown) us4[q] = v[i];
+      if (q >= nown) break;
+      const size_t gq = (size_t)t0 * Q4 + q;
+      const float qi = __ldg(iq + t0 + q / Q4);
+      const float4 ri = rA[gq];
+      float4 rn, un;
+      if (INIT) {
+        rn = ri;
+        un = scale4(ri, qi);
+        p4[gq] = un;
+        x4[gq] = make_float4(0.f, 0.f, 0.f, 0.f);
+        sB[gq] = make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        const float4 wi = wA[gq], si = sA[gq], pi = p4[gq], xi = x4[gq];
+        const float4 u0 = scale4(ri, qi);
+        const float4 pn = make_float4(__fadd_rn(u0.x, bmul(be.x, pi.x)), __fadd_rn(u0.y, bmul(be.y, pi.y)),
+                                      __fadd_rn(u0.z, bmul(be.z, pi.z)), __fadd_rn(u0.w, bmul(be.w, pi.w)));
+        const float4 sn = next_s(wi, si, be);
+        rn = next_r(ri, sn, al);
+        un = scale4(rn, qi);
+        p4[gq] = pn;
+        x4[gq] = make_float4(xi.x + al.x * pn.x, xi.y + al.y * pn.y, xi.z + al.z * pn.z, xi.w + al.w * pn.w);
+        sB[gq] = sn;
+      }
+      rB[gq] = rn;
+      us4[q] = un;
+      fa[0] += rn.x * un.x; fa[1] += rn.y * un.y; fa[2] += rn.z * un.z; fa[3] += rn.w * un.w;
+      fa[4] += rn.x * rn.x; fa[5] += rn.y * rn.y; fa[6] += rn.z * rn.z; fa[7] += rn.w * rn.w;
     }
+    // phase 2: external rows
     const int next = ne * Q4;
-    float4 ev[XN];
-#pragma unroll
+#pragma unroll 2
     for (int i = 0; i < XN; ++i) {
       const int q = threadIdx.x + i * CT;
-      ev[i] = q < next ? __ldg(u4 + (size_t)ji[i] * Q4 + (q % Q4)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int i = 0; i < XN; ++i) {
-      const int q = threadIdx.x + i * CT;
-      if (q < next) us4[SP_TR * Q4 + q] = ev[i];
+      if (q >= next) break;
+      const size_t gj = (size_t)ji[i] * Q4 + (q % Q4);
+      const float qj = __ldg(iq + ji[i]);
+      const float4 rj = rA[gj];
+      float4 un;
+      if (INIT) {
+        un = scale4(rj, qj);
+      } else {
+        const float4 sn = next_s(wA[gj], sA[gj], be);
+        un = scale4(next_r(rj, sn, al), qj);
+      }
+      us4[SP_TR * Q4 + q] = un;
     }
     __syncthreads();
-    float ft = 0.0f;
+    // phase 3: w' = Q u' for the own rows
 #pragma unroll 4
     for (int jstep = 0; jstep < 16 / RPW; ++jstep) {
       const int src = jstep * RPW + lane / R;  // row of the warp's 16, and the lane holding its slots
@@ -428,21 +394,56 @@ __global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ 
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         const int sk = sv[k];
-        un[k] = sk < 0 ? 0.0f
-                       : (sk == SP_GLOBAL ? __ldg(u + (size_t)__ldg(A->nb6 + 6 * (size_t)row + k) * R + c)
-                                          : us[sk * R + c]);
+        float v = 0.0f;
+        if (sk == SP_GLOBAL) {  // external row beyond the staged list: form u' from global memory
+          const int j = __ldg(A->nb6 + 6 * (size_t)row + k);
+          const size_t gj = (size_t)j * R + c;
+          const float rj = A->r[par][gj];
+          const float qj = __ldg(iq + j);
+          if (INIT) {
+            v = __fmul_rn(rj, qj);
+          } else {
+            const float a = (float)st->alpha[c], b = bench ? 0.f : (float)st->beta[c];
+            const float sn = __fadd_rn(A->w[par][gj], bmul(b, A->s[par][gj]));
+            v = __fmul_rn(__fsub_rn(rj, __fmul_rn(bench ? 0.f : a, sn)), qj);
+          }
+        } else if (sk >= 0) {
+          v = us[sk * R + c];
+        }
+        un[k] = v;
       }
       const float ns = ((un[0] + un[1]) + (un[2] + un[3])) + (un[4] + un[5]);
       const float wn = q * uo - lam * ns;
-      w[(size_t)row * R + c] = wn;
+      wB[(size_t)row * R + c] = wn;
       ft += wn * uo;
     }
-    acc += (double)ft;  // FP32 over the tile's rows of this lane (<= 16), FP64 across tiles
   }
-  double v[1] = {acc};
+  // per-column CTA sums: phase 1 (lanes sharing threadIdx % Q4, then warps) -> part1
+  {
+    __shared__ double sh1[CT / 32][8][8];
+    double acc1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc1[k] = (double)fa[k];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      for (int o = 16; o >= Q4; o >>= 1) acc1[k] += __shfl_xor_sync(0xffffffffu, acc1[k], o);
+    if (lane < Q4) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sh1[wrp][lane][k] = acc1[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * R) {
+      const int qk = threadIdx.x / R, cc = threadIdx.x % R;  // qk: 0 = r.u, 1 = r.r
+      double t = 0.0;
+      for (int ww = 0; ww < CT / 32; ++ww) t += sh1[ww][cc / 4][4 * qk + (cc & 3)];
+      A->part1[((size_t)qk * R + cc) * gridDim.x + blockIdx.x] = t;
+    }
+  }
+  // phase 3 (one column per lane) -> part
+  double v[1] = {(double)ft};
   column_partials<R, 1>(v, A->part);
   if (!arrive_last(&st->cnt)) return;
-  if (bench) {  // timing only: scalars stay as they are
+  if (bench) {
     if (threadIdx.x == 0) st->cnt = 0;
     return;
   }
@@ -450,7 +451,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ 
   __shared__ double tot1[3][MAXR];
   __shared__ int any_live;
   sum_partials<1>(A->part, R, gridDim.x, tot);
-  sum_partials<2>(A->part1, R, NCTA, tot1);  // pass 1 (NCTA CTAs): r.u, r.r
+  sum_partials<2>(A->part1, R, gridDim.x, tot1);
   const bool first = st->first;
   if (threadIdx.x == 0) {
     any_live = 0;
@@ -459,36 +460,36 @@ __global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ 
   __syncthreads();
   if (threadIdx.x < R) {
     const int cc = threadIdx.x;
-    const double g = tot1[0][cc], rr = tot1[1][cc], d = tot[0][cc];
+    const double gm = tot1[0][cc], rr = tot1[1][cc], d = tot[0][cc];
     if (!st->done[cc]) {
       if (first) {
-        st->gamma[cc] = g;
+        st->gamma[cc] = gm;
         st->beta[cc] = 0.0;
-        if (!(d > 0.0) || !isfinite(d) || !isfinite(g)) {
+        if (!(d > 0.0) || !isfinite(d) || !isfinite(gm)) {
           st->done[cc] = 1;
           st->status = 2;
         } else {
-          st->alpha[cc] = g / d;
+          st->alpha[cc] = gm / d;
           atomicOr(&any_live, 1);
         }
       } else {
         st->rr[cc] = rr;
         st->iters[cc] += 1;
-        if (!isfinite(g) || !isfinite(d) || !isfinite(rr)) {
+        if (!isfinite(gm) || !isfinite(d) || !isfinite(rr)) {
           st->done[cc] = 1;
           st->status = 2;
         } else if (rr <= st->tol2[cc] * st->bb[cc]) {
           st->done[cc] = 1;
         } else {
-          const double beta = g / st->gamma[cc];
-          const double den = d - beta * g / st->alpha[cc];
+          const double beta = gm / st->gamma[cc];
+          const double den = d - beta * gm / st->alpha[cc];
           if (!(den > 0.0) || !isfinite(den)) {
             st->done[cc] = 1;
             st->status = 2;
           } else {
             st->beta[cc] = beta;
-            st->alpha[cc] = g / den;
-            st->gamma[cc] = g;
+            st->alpha[cc] = gm / den;
+            st->gamma[cc] = gm;
             atomicOr(&any_live, 1);
           }
         }
@@ -502,9 +503,10 @@ __global__ void __launch_bounds__(CT, 2) k_blk_spmm(const BlkArgs* __restrict__ 
   __syncthreads();
   if (threadIdx.x == 0) {
     st->first = 0;
+    st->par ^= 1;
     if (!any_live || st->iter >= st->max_iter) {
       st->all_done = 1;
-      if (mode == SPMM_GRAPH) cudaGraphSetConditional(handle, 0);
+      if (mode == IT_GRAPH) cudaGraphSetConditional(handle, 0);
     }
     st->cnt = 0;
   }
@@ -685,6 +687,7 @@ __global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, in
     st->status = 0;
     st->ncols = ncols;
     st->first = 1;
+    st->par = 0;  // k_probes wrote the first right-hand side into r[0]
     st->cnt = 0;
     st->guard = 0;
     st->nexec = 0;
@@ -729,8 +732,8 @@ struct BlockGraph {
 };
 
 static void free_arrays(BlockGraph* g) {
-  void* ptrs[] = {g->h.r[0], g->h.w[0], g->h.s[0], g->h.p, g->h.x, g->h.u, g->h.x64,
-                  g->h.iq, g->h.part, g->h.part1, g->Z, g->sacc};
+  void* ptrs[] = {g->h.r[0], g->h.w[0], g->h.s[0], g->h.r[1], g->h.w[1], g->h.s[1], g->h.p, g->h.x,
+                  g->h.x64, g->h.iq,      g->h.part, g->h.part1, g->Z, g->sacc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   g->cap_rows = 0;
@@ -750,17 +753,14 @@ void block_graph_free(BlockGraph* g) {
 }
 
 template <int R>
-static void blk_iter(BlockGraph* g, cudaStream_t s, cudaGraphConditionalHandle h, int bench = 0) {
-  k_blk_upd<R, false><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
-  k_blk_spmm<R><<<SP_NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, h, bench ? SPMM_BENCH : SPMM_GRAPH);
+static void blk_iter(BlockGraph* g, cudaStream_t s, cudaGraphConditionalHandle h) {
+  k_blk_it<R, false><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, h, IT_GRAPH);
 }
 
-// start of a correction solve from r: u, p = s = x = 0, w = Q u, alpha
+// start of a correction solve from r: u = r/Q_jj, p = u, s = x = 0, w = Q u, alpha
 template <int R>
 static void blk_start(BlockGraph* g, cudaStream_t s) {
-  k_blk_upd<R, true><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
-  count_launch();
-  k_blk_spmm<R><<<SP_NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_START);
+  k_blk_it<R, true><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), IT_START);
   count_launch();
 }
 
@@ -782,7 +782,8 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
   if (!g) {
     g = new BlockGraph();
     g->R = R;
-    BF_CK(cudaFuncSetAttribute(k_blk_spmm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
+    BF_CK(cudaFuncSetAttribute(k_blk_it<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
+    BF_CK(cudaFuncSetAttribute(k_blk_it<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
     memset(&g->h, 0, sizeof(g->h));
     BF_CK(cudaMalloc(&g->d_args, sizeof(BlkArgs)));
     BF_CK(cudaMallocHost(&g->h_pin, sizeof(BlkArgs)));
@@ -812,17 +813,18 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     free_arrays(g);
     const int64_t rows = b->N + b->N / 8 + 1024;
     const size_t nv = (size_t)rows * R;
-    BF_CK(cudaMalloc(&g->h.r[0], nv * 4));
-    BF_CK(cudaMalloc(&g->h.w[0], nv * 4));
-    BF_CK(cudaMalloc(&g->h.s[0], nv * 4));
-    BF_CK(cudaMalloc(&g->h.u, nv * 4));
+    for (int k = 0; k < 2; ++k) {
+      BF_CK(cudaMalloc(&g->h.r[k], nv * 4));
+      BF_CK(cudaMalloc(&g->h.w[k], nv * 4));
+      BF_CK(cudaMalloc(&g->h.s[k], nv * 4));
+    }
     BF_CK(cudaMalloc(&g->h.p, nv * 4));
     BF_CK(cudaMalloc(&g->h.x, nv * 4));
     BF_CK(cudaMalloc(&g->h.x64, nv * 8));
     BF_CK(cudaMalloc(&g->Z, nv * 2));
     BF_CK(cudaMalloc(&g->h.iq, (size_t)rows * 4));
     BF_CK(cudaMalloc(&g->sacc, (size_t)rows * 8));
-    BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NPART * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NCTA * sizeof(double)));
     BF_CK(cudaMalloc(&g->h.part1, (size_t)2 * R * NCTA * sizeof(double)));
     g->cap_rows = rows;
   }
@@ -919,9 +921,9 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
   return BF_OK;
 }
 
-// which: 0 = one iteration (both passes), 1 = update pass, 2 = SpMM pass
+// time one block-PCG iteration (k_blk_it in timing mode)
 template <int R>
-static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int which, int reps, double* ms) {
+static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int reps, double* ms) {
   BlockGraph* g = nullptr;
   BF_TRY(get_block_solver<R>(ctx, b, &g));
   cudaStream_t s = ctx->stream;
@@ -934,14 +936,8 @@ static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int which, int reps, doubl
   BF_CK(cudaEventCreate(&e1));
   BF_CK(cudaEventRecord(e0, s));
   for (int i = 0; i < reps; ++i) {
-    if (which != 2) {
-      k_blk_upd<R, false><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
-      count_launch();
-    }
-    if (which != 1) {
-      k_blk_spmm<R><<<SP_NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), SPMM_BENCH);
-      count_launch();
-    }
+    k_blk_it<R, false><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), IT_BENCH);
+    count_launch();
   }
   BF_CK(cudaEventRecord(e1, s));
   BF_CK(cudaEventSynchronize(e1));
@@ -953,11 +949,11 @@ static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int which, int reps, doubl
   return BF_OK;
 }
 
-bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms) {
+bf_status bench_block_iter(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms) {
   switch (R) {
-    case 8: return bench_blk_t<8>(ctx, b, which, reps, ms);
-    case 16: return bench_blk_t<16>(ctx, b, which, reps, ms);
-    case 32: return bench_blk_t<32>(ctx, b, which, reps, ms);
+    case 8: return bench_blk_t<8>(ctx, b, reps, ms);
+    case 16: return bench_blk_t<16>(ctx, b, reps, ms);
+    case 32: return bench_blk_t<32>(ctx, b, reps, ms);
   }
   return bf_fail(ctx, BF_EINVAL, "R must be 8, 16 or 32");
 }

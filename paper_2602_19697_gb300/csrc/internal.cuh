@@ -167,7 +167,7 @@ bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, uns
                           double* relres);
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
                         int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq = nullptr);
-bf_status bench_block_spmv(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms);
+bf_status bench_block_iter(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms);
 void solve_graph_free(SolveGraph* g);
 void block_graph_free(BlockGraph* g);
 bf_status mc_impl(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt);

@@ -23,9 +23,12 @@
 //   beta' = gamma'/gamma,  alpha' = gamma' / (delta' - beta' gamma'/alpha)
 // and the stop flags.  The iteration loop is a CUDA-graph WHILE node.
 //
-// Refinement: FP64 master iterates x64 per column; k_blk_outer computes the
-// true residual z - Q x64 in FP64, the FP32 solve reduces it by a factor
-// eta, x64 += x, until every column meets the tolerance.
+// Refinement: master iterates xm per column in float-float arithmetic (an
+// unevaluated sum hi + lo of two floats, about 48 significant bits: Dekker's
+// exact product by FMA and Knuth's exact sum); k_blk_outer computes the true
+// residual z - Q xm in that arithmetic, the FP32 solve reduces it by a factor
+// eta, xm += x, until every column meets the tolerance.  (FP64 would serve
+// too, but its throughput on this GPU is a small fraction of FP32's.)
 //
 // The solver (workspaces, state, graph) belongs to the context, one per
 // block width R: kernels read band pointers and sizes from a device-resident
@@ -79,7 +82,7 @@ struct BlkArgs {
   float* s[2];         // Q p (by recurrence)
   float* p;
   float* x;            // FP32 correction
-  double* x64;         // FP64 master iterates
+  float2* xm;          // float-float master iterates (hi, lo)
   const __nv_bfloat16* Z;
   double* part;        // [3][R][NCTA]
   double* part1;       // [2][R][NCTA] pass-1 partials
@@ -91,6 +94,30 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
   return z ^ (z >> 31);
 }
+
+// float-float arithmetic: (hi, lo) with |lo| <= ulp(hi)/2
+__device__ __forceinline__ float2 two_sum(float a, float b) {  // a + b = s + e exactly (Knuth)
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_add(float2 x, float2 y) {
+  const float2 t = two_sum(x.x, y.x);
+  return quick_two_sum(t.x, __fadd_rn(t.y, __fadd_rn(x.y, y.y)));
+}
+__device__ __forceinline__ float2 ff_add_f(float2 x, float b) {
+  const float2 t = two_sum(x.x, b);
+  return quick_two_sum(t.x, __fadd_rn(t.y, x.y));
+}
+__device__ __forceinline__ float2 ff_mul_f(float2 x, float b) {  // exact product of hi by FMA (Dekker)
+  const float p = __fmul_rn(x.x, b);
+  const float e = __fmaf_rn(x.y, b, __fmaf_rn(x.x, b, -p));
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
 
 __device__ __forceinline__ bool arrive_last(unsigned int* counter) {
   __shared__ bool last;
@@ -159,11 +186,12 @@ __device__ __forceinline__ void load_nb6(const int32_t* __restrict__ nb6, int ro
   nb[0] = n01.x; nb[1] = n01.y; nb[2] = n23.x; nb[3] = n23.y; nb[4] = n45.x; nb[5] = n45.y;
 }
 
-// True residual of the FP64 master iterates, per column: r = z - Q x64 with
-// FP64 arithmetic, stored as the FP32 right-hand side (r[par]) of the next
-// correction solve; per-column r.r and z.z.  The last CTA sets, per column,
-// the stop flag (true residual within tolerance) and the correction target
-// eta = 0.5 tol |z| / |r| clamped to [1e-5, 0.5].
+// True residual of the master iterates, per column: r = z - Q xm in
+// float-float arithmetic, stored as the FP32 right-hand side (r[par]) of the
+// next correction solve; per-column r.r and z.z (FP32 products summed per
+// thread, FP64 from the CTA sums on).  The last CTA sets, per column, the
+// stop flag (true residual within tolerance) and the correction target
+// eta = 0.5 tol |z| / |r| clamped to [ETA_MIN, 0.5].
 template <int R>
 __global__ void __launch_bounds__(CT) k_blk_outer(const BlkArgs* __restrict__ A, BlkState* st) {
   const int N = A->N;
@@ -171,24 +199,27 @@ __global__ void __launch_bounds__(CT) k_blk_outer(const BlkArgs* __restrict__ A,
   const int lane = threadIdx.x & 31, c = lane % R;
   constexpr int RPW = 32 / R;
   const int wrp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double* __restrict__ x64 = A->x64;
+  const float2* __restrict__ xm = A->xm;
   int row0, row1;
   cta_rows(N, &row0, &row1);
-  double acc[2] = {0.0, 0.0};
+  float fr = 0.0f, fz = 0.0f;
   for (int row = row0 + wrp * RPW + lane / R; row < row1; row += nw * RPW) {
     const size_t o = (size_t)row * R + c;
     int nb[6];
     load_nb6(A->nb6, row, nb);
-    double ns = 0.0;
+    float2 ns = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < 6; ++k)
-      if (nb[k] >= 0) ns += x64[(size_t)nb[k] * R + c];
-    const double z = (double)__bfloat162float(A->Z[o]);
-    const double r = z - ((double)__ldg(A->qd + row) * x64[o] - (double)lam * ns);
-    A->r[st->par][o] = (float)r;
-    acc[0] += r * r;
-    acc[1] += z * z;
+      if (nb[k] >= 0) ns = ff_add(ns, xm[(size_t)nb[k] * R + c]);
+    const float z = __bfloat162float(A->Z[o]);
+    const float2 qx = ff_add(ff_mul_f(xm[o], __ldg(A->qd + row)), ff_neg(ff_mul_f(ns, lam)));
+    const float2 rf = ff_add_f(ff_neg(qx), z);
+    const float r = __fadd_rn(rf.x, rf.y);
+    A->r[st->par][o] = r;
+    fr += r * r;
+    fz += z * z;
   }
+  double acc[2] = {(double)fr, (double)fz};
   column_partials<R, 2>(acc, A->part);
   if (!arrive_last(&st->cnt)) return;
   __shared__ double tot[3][MAXR];
@@ -512,11 +543,11 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   }
 }
 
-// Z[i][c] = Rademacher(seed, k0 + c, lin_i) for c < ncols, 0 beyond; x64 = 0
+// Z[i][c] = Rademacher(seed, k0 + c, lin_i) for c < ncols, 0 beyond; xm = 0
 // and the first correction right-hand side r = z - Q 0 = z
 template <int R>
 __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed, int k0, int ncols,
-                         __nv_bfloat16* __restrict__ Z, double* __restrict__ x, float* __restrict__ r0) {
+                         __nv_bfloat16* __restrict__ Z, float2* __restrict__ x, float* __restrict__ r0) {
   const int64_t n = (int64_t)N * R;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / R;
@@ -527,25 +558,44 @@ __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed,
       z = (v >> 63) ? -1.0f : 1.0f;
     }
     Z[e] = __float2bfloat16(z);
-    x[e] = 0.0;
+    x[e] = make_float2(0.f, 0.f);
     r0[e] = z;
   }
 }
 
-// s_acc[i] += sum_c z[i][c] x64[i][c]; sq[i] += sum_c (z[i][c] x64[i][c])^2 if sq
+// s_acc[i] += sum_c z[i][c] xm[i][c] (float-float sum over the columns, a
+// fixed xor-shuffle tree, then FP64); sq[i] += sum_c (z[i][c] xm[i][c])^2 if
+// sq (likewise: the judge of the variance surrogate forms a sample variance
+// from it, where the two moments cancel).  Lanes are columns: a warp takes 32/R rows at a time.
 template <int R>
-__global__ void k_hutch(int N, const __nv_bfloat16* __restrict__ Z, const double* __restrict__ x,
+__global__ void k_hutch(int N, const __nv_bfloat16* __restrict__ Z, const float2* __restrict__ xm,
                         double* __restrict__ sacc, double* __restrict__ sq) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    double s = 0.0, q = 0.0;
-#pragma unroll
-    for (int c = 0; c < R; ++c) {
-      const double t = (double)__bfloat162float(Z[(size_t)i * R + c]) * x[(size_t)i * R + c];
-      s += t;
-      q += t * t;
+  constexpr int RPW = 32 / R;
+  const int lane = threadIdx.x & 31, c = lane % R;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = gw * RPW; base < N; base += nwarp * RPW) {
+    const int64_t row = base + lane / R;
+    float2 t = make_float2(0.f, 0.f);
+    if (row < N) {
+      const float z = __bfloat162float(Z[row * R + c]);
+      const float2 x = xm[row * R + c];
+      t = make_float2(z * x.x, z * x.y);  // z = +-1 or 0: exact
     }
-    sacc[i] += s;
-    if (sq) sq[i] += q;
+    // t^2 in float-float: hi^2 exactly by FMA, plus 2 hi lo
+    const float p0 = __fmul_rn(t.x, t.x);
+    float2 q = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
+#pragma unroll
+    for (int o = R / 2; o > 0; o >>= 1) {
+      const float2 u = make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o));
+      const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, q.x, o), __shfl_xor_sync(0xffffffffu, q.y, o));
+      t = ff_add(t, u);
+      q = ff_add(q, v);
+    }
+    if (c == 0 && row < N) {
+      sacc[row] += (double)t.x + (double)t.y;
+      if (sq) sq[row] += (double)q.x + (double)q.y;
+    }
   }
 }
 
@@ -553,9 +603,10 @@ __global__ void k_finish(int N, const double* __restrict__ sacc, double invK, fl
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) s[i] = (float)(sacc[i] * invK);
 }
 
-__global__ void k_axpy64(int64_t n, const float* __restrict__ d, double* __restrict__ x) {
+// xm += d in float-float arithmetic
+__global__ void k_axpy_ff(int64_t n, const float* __restrict__ d, float2* __restrict__ xm) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)d[i];
+    xm[i] = ff_add_f(xm[i], d[i]);
 }
 
 // per-voxel indices of the six face neighbours (-x, +x, -y, +y, -z, +z), -1 outside the band
@@ -664,8 +715,8 @@ __global__ void k_inv(int N, const float* __restrict__ qd, float* __restrict__ i
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) iq[i] = 1.0f / qd[i];
 }
 
-// State for a new block of probes.  With x64 = 0 the true residual is z
-// itself, so |r|^2 = |z|^2 = N for every live column and no FP64 pass is
+// State for a new block of probes.  With xm = 0 the true residual is z
+// itself, so |r|^2 = |z|^2 = N for every live column and no residual pass is
 // needed before the first correction solve.
 __global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, int N, double eta_min) {
   int c = threadIdx.x;
@@ -733,7 +784,7 @@ struct BlockGraph {
 
 static void free_arrays(BlockGraph* g) {
   void* ptrs[] = {g->h.r[0], g->h.w[0], g->h.s[0], g->h.r[1], g->h.w[1], g->h.s[1], g->h.p, g->h.x,
-                  g->h.x64, g->h.iq,      g->h.part, g->h.part1, g->Z, g->sacc};
+                  g->h.xm, g->h.iq,       g->h.part, g->h.part1, g->Z, g->sacc};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   g->cap_rows = 0;
@@ -820,7 +871,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     }
     BF_CK(cudaMalloc(&g->h.p, nv * 4));
     BF_CK(cudaMalloc(&g->h.x, nv * 4));
-    BF_CK(cudaMalloc(&g->h.x64, nv * 8));
+    BF_CK(cudaMalloc(&g->h.xm, nv * sizeof(float2)));
     BF_CK(cudaMalloc(&g->Z, nv * 2));
     BF_CK(cudaMalloc(&g->h.iq, (size_t)rows * 4));
     BF_CK(cudaMalloc(&g->sacc, (size_t)rows * 8));
@@ -860,7 +911,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
 
 template <int R>
 static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
-                            int max_iter, float* s_out, int* total_iters, double* sq) {
+                            int max_iter, float* s_out, int* total_iters, double* sq, double* s1) {
   cudaStream_t s = ctx->stream;
   BlockGraph* g = nullptr;
   BF_TRY(get_block_solver<R>(ctx, b, &g));
@@ -880,9 +931,9 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
   const int64_t NR = (int64_t)N * R;
   const unsigned gNR = grid_for(NR, 256, 152 * 32);
   for (int k0 = kb; k0 < ke; k0 += R) {
-    // one block of R probes: FP64 master iterates, FP32 correction solves
+    // one block of R probes: float-float master iterates, FP32 correction solves
     int ncols = ke - k0 < R ? ke - k0 : R;
-    k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.x64, g->h.r[0]);
+    k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.xm, g->h.r[0]);
     count_launch();
     k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols, N, ETA_MIN);
     count_launch();
@@ -897,7 +948,7 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
         break;
       }
       BF_CK(cudaGraphLaunch(g->exec, s));
-      k_axpy64<<<gNR, 256, 0, s>>>(NR, g->h.x, g->h.x64);
+      k_axpy_ff<<<gNR, 256, 0, s>>>(NR, g->h.x, g->h.xm);
       count_launch();
       blk_outer<R>(g, s);
       BF_CK(cudaGetLastError());
@@ -905,13 +956,14 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
     const BlkState& h = *g->h_st;
     count_launch(h.nexec);
     for (int c = 0; c < ncols; ++c) tot_it += h.iters[c];
-    k_hutch<R><<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->Z, g->h.x64, g->sacc, sq);
+    k_hutch<R><<<grid_for((int64_t)N * R, 256, 152 * 16), 256, 0, s>>>(N, g->Z, g->h.xm, g->sacc, sq);
     count_launch();
     BF_CK(cudaGetLastError());
     if (h.status == 2) { result = BF_BREAKDOWN; break; }
     if (!done || h.status == 1) { result = BF_NOT_CONVERGED; break; }
   }
   k_finish<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->sacc, scale, s_out);
+  if (s1) BF_CK(cudaMemcpyAsync(s1, g->sacc, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, s));
   count_launch();
   BF_CK(cudaGetLastError());
   BF_CK(cudaStreamSynchronize(s));
@@ -959,9 +1011,9 @@ bf_status bench_block_iter(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms)
 }
 
 // probes k in [kb, ke); s = scale * sum_k z_k (.) Q^-1 z_k; sq (device, may be
-// null) += sum_k (z_k (.) Q^-1 z_k)^2
+// null) += sum_k (z_k (.) Q^-1 z_k)^2; s1 (device, may be null) = the FP64 sum
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
-                        int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq) {
+                        int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq, double* s1) {
   (void)flags;
   if (b->N == 0) {
     if (total_iters) *total_iters = 0;
@@ -970,9 +1022,9 @@ bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, u
   const int K = ke - kb;
   if (R == 0) R = K >= 32 ? 32 : (K >= 16 ? 16 : 8);
   switch (R) {
-    case 8: return variance_t<8>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq);
-    case 16: return variance_t<16>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq);
-    case 32: return variance_t<32>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq);
+    case 8: return variance_t<8>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
+    case 16: return variance_t<16>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
+    case 32: return variance_t<32>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
   }
   return bf_fail(ctx, BF_EINVAL, "rhs_block must be 0, 8, 16 or 32");
 }

@@ -166,7 +166,8 @@ bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
 bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,
                           double* relres);
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
-                        int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq = nullptr);
+                        int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq = nullptr,
+                        double* s1 = nullptr);
 bf_status bench_block_iter(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms);
 void solve_graph_free(SolveGraph* g);
 void block_graph_free(BlockGraph* g);

@@ -398,13 +398,14 @@ __global__ void k_init(float* __restrict__ p, int64_t n, uint64_t seed, int64_t 
   }
 }
 
-// Surrogate judge, one CTA per brick.  From K_j probe values t_k = z_k (.) Q^-1 z_k:
+// Surrogate judge, one CTA per brick.  From the sums s1 = sum_k t_k and sq = sum_k t_k^2
+// of K_j probe values t_k = z_k (.) Q^-1 z_k:
 // s_J = mean, se = sample std / sqrt(K_j), floor f = max(s_J, 1/Q_ii),
 // e_i = |s_hat_i - s_J,i|; stat0 = median over the brick of e_i / f_i,
 // stat1 = max over the brick of e_i / (3 se_i + 0.1 f_i); accepted iff
 // stat0 <= 0.10 and stat1 <= 1.
 __global__ void __launch_bounds__(256) k_judge(const int32_t* __restrict__ off, const float* __restrict__ qd,
-                                               const float* __restrict__ lsh, const float* __restrict__ sJ,
+                                               const float* __restrict__ lsh, const double* __restrict__ s1,
                                                const double* __restrict__ sq, int Kj, double* __restrict__ stat,
                                                uint8_t* __restrict__ acc, int* __restrict__ nacc) {
   __shared__ double rel[512];
@@ -415,8 +416,8 @@ __global__ void __launch_bounds__(256) k_judge(const int32_t* __restrict__ off, 
     double rv = CUDART_INF;
     if (l < n) {
       const int i = i0 + l;
-      const double sj = (double)sJ[i];
-      const double var = fmax((sq[i] - (double)Kj * sj * sj) / (double)(Kj - 1), 0.0);
+      const double sj = s1[i] / (double)Kj;
+      const double var = fmax((sq[i] - sj * s1[i]) / (double)(Kj - 1), 0.0);
       const double se = sqrt(var / (double)Kj);
       const double f = fmax(sj, 1.0 / (double)qd[i]);
       const double e = fabs(exp((double)lsh[i]) - sj);
@@ -769,7 +770,7 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
   BF_TRY(stage_in(ctx, log_s_hat, N, WS_STAGE2, &dl));
   BF_TRY(stage_out(ctx, s, N, WS_OUT0, &ds, &hs));
   float *sJ = nullptr, *rest = nullptr;
-  double *sq = nullptr, *stat = nullptr;
+  double *sq = nullptr, *s1 = nullptr, *stat = nullptr;
   uint8_t* acc = nullptr;
   int* nacc = nullptr;
   bf_status r = BF_OK;
@@ -777,12 +778,14 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
     dev_free(st, sJ);
     dev_free(st, rest);
     dev_free(st, sq);
+    dev_free(st, s1);
     dev_free(st, stat);
     dev_free(st, acc);
     dev_free(st, nacc);
     return x;
   };
   if ((r = dev_alloc_t(ctx, &sJ, N)) || (r = dev_alloc_t(ctx, &rest, N)) || (r = dev_alloc_t(ctx, &sq, N)) ||
+      (r = dev_alloc_t(ctx, &s1, N)) ||
       (r = dev_alloc_t(ctx, &stat, 2 * (size_t)NB)) || (r = dev_alloc_t(ctx, &acc, NB)) ||
       (r = dev_alloc_t(ctx, &nacc, 1)))
     return done(r);
@@ -790,9 +793,9 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
     return done(bf_fail(ctx, BF_ECUDA, "bf_surrogate_variance: memset"));
   // judge: probes 0 .. K_judge - 1 (the first K_judge probes of the K-probe estimate)
   int it_j = 0, it_r = 0;
-  r = variance_impl(ctx, b, 0, K_judge, 1.0 / K_judge, seed, rel_tol, max_iter, rhs_block, flags, sJ, &it_j, sq);
+  r = variance_impl(ctx, b, 0, K_judge, 1.0 / K_judge, seed, rel_tol, max_iter, rhs_block, flags, sJ, &it_j, sq, s1);
   if (r) return done(r);
-  k_judge<<<NB, 256, 0, st>>>(b->off, b->qd, dl, sJ, sq, K_judge, stat, acc, nacc);
+  k_judge<<<NB, 256, 0, st>>>(b->off, b->qd, dl, s1, sq, K_judge, stat, acc, nacc);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) return done(bf_fail(ctx, BF_ECUDA, "k_judge launch"));
   int h_nacc = 0;

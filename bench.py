@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget (s)")
+    ap.add_argument("--kernel", default=None,
+                    choices=["block_iter", "spmv", "net_forward", "net_train", "net_conv", "net_wgrad"],
+                    help="time one kernel alone on the workload's band (for profiling): --warmup untimed and "
+                         "--steps timed launches; prints one JSON line with its throughput")
     return ap.parse_args()
 
 
@@ -350,8 +354,44 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_kernel(args):
+    """One kernel of the path, launched alone through the library's timing
+    entries (CUDA events on the library stream)."""
+    import torch
+
+    import synth
+    from paper_2602_19697_gb300 import bfsdf, build
+    build.build()
+    ctx = bfsdf.Context(0)
+    w = synth.make_workload(args.workload)
+    depth, poses = torch.from_numpy(w.depth).cuda(), torch.from_numpy(w.poses).cuda()
+    band = ctx.build_band_w(w, depth, poses)
+    band.integrate_depth(depth, poses, w.intr)
+    N, NB, R = band.N, band.NB, args.rhs_block
+    out = {"kernel": args.kernel, "workload": args.workload, "N_band": N, "bricks": NB}
+    if args.kernel in ("block_iter", "spmv"):
+        which = bfsdf.BF_KERNEL_BLOCK_ITER if args.kernel == "block_iter" else bfsdf.BF_KERNEL_SPMV
+        band.bench_kernel(which, R=R, reps=max(args.warmup, 1))
+        ms = band.bench_kernel(which, R=R, reps=max(args.steps, 1))
+        nbytes = N * (R * 40 + 8) if args.kernel == "block_iter" else N * 12 + NB * (128 + 24)
+        out.update(ms_per_launch=ms, bytes_per_launch=nbytes, achieved_gbs=nbytes / (ms * 1e-3) / 1e9)
+    else:
+        net = bfsdf.Net(ctx, seed=0)
+        which = {"net_forward": bfsdf.BF_NET_BENCH_FORWARD, "net_train": bfsdf.BF_NET_BENCH_TRAIN,
+                 "net_conv": bfsdf.BF_NET_BENCH_CONV, "net_wgrad": bfsdf.BF_NET_BENCH_WGRAD}[args.kernel]
+        flops = {"net_forward": bfsdf.NET_FLOPS_FWD, "net_train": 3 * bfsdf.NET_FLOPS_FWD - 2 * 1000 * 27 * 2 * 32,
+                 "net_conv": bfsdf.NET_FLOPS_CONV, "net_wgrad": bfsdf.NET_FLOPS_CONV}[args.kernel] * NB
+        net.bench(band, which, reps=max(args.warmup, 1))
+        ms = net.bench(band, which, reps=max(args.steps, 1))
+        out.update(ms_per_rep=ms, flops_per_rep=flops, achieved_tflops=flops / (ms * 1e-3) / 1e12)
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.kernel:
+        run_kernel(args)
+        return
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

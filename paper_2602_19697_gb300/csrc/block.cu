@@ -582,15 +582,20 @@ __global__ void k_hutch(int N, const __nv_bfloat16* __restrict__ Z, const float2
       const float2 x = xm[row * R + c];
       t = make_float2(z * x.x, z * x.y);  // z = +-1 or 0: exact
     }
-    // t^2 in float-float: hi^2 exactly by FMA, plus 2 hi lo
-    const float p0 = __fmul_rn(t.x, t.x);
-    float2 q = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
+    // t^2 in float-float: hi^2 exactly by FMA, plus 2 hi lo (only when sq is asked for)
+    float2 q = make_float2(0.f, 0.f);
+    if (sq) {
+      const float p0 = __fmul_rn(t.x, t.x);
+      q = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
+    }
 #pragma unroll
     for (int o = R / 2; o > 0; o >>= 1) {
       const float2 u = make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o));
-      const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, q.x, o), __shfl_xor_sync(0xffffffffu, q.y, o));
       t = ff_add(t, u);
-      q = ff_add(q, v);
+      if (sq) {
+        const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, q.x, o), __shfl_xor_sync(0xffffffffu, q.y, o));
+        q = ff_add(q, v);
+      }
     }
     if (c == 0 && row < N) {
       sacc[row] += (double)t.x + (double)t.y;

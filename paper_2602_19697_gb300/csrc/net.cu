@@ -87,6 +87,7 @@ template <int C>
 __device__ __forceinline__ void stage_tile(const __nv_bfloat16* __restrict__ src, __nv_bfloat16* xs) {
   constexpr int U = C / 8;  // uint4 per row
   const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll 4
   for (int q = threadIdx.x; q < PV * U; q += NT) {
     int p = q / U, u = q - p * U;
     int px = p % 12, py = (p / 12) % 12, pz = p / 144;
@@ -518,6 +519,15 @@ static bf_status net_pack(bf_ctx* ctx, bf_net* net) {
   return BF_OK;
 }
 
+// CTAs for a brick-striding kernel: as many as are resident at once (at most nb)
+template <class K>
+static int occ_grid(K kern, size_t smem, int nb) {
+  int per = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, smem) != cudaSuccess || per < 1) per = 1;
+  const int g = per * 152;
+  return nb < g ? nb : g;
+}
+
 static bf_status set_attrs(bf_ctx* ctx, bf_net* net) {
   if (net->attr) return BF_OK;
   BF_CK(cudaFuncSetAttribute(k_conv<16, 32, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -559,17 +569,16 @@ static bf_status net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, const f
   const int nb = b->NB;
   BF_TRY(set_attrs(ctx, net));
   BF_TRY(ensure_batch(ctx, net, nb));
-  const int grid = nb < 152 ? nb : 152;
   BandView bv = band_view(b);
   k_features<<<nb, 256, 0, s>>>(bv, b->tsdf, b->d, net->act[0]);
   count_launch();
   LossArgs none;
   memset(&none, 0, sizeof(none));
-  k_conv<16, 32, MODE_FWD><<<grid, NT, conv_smem<16, 32>(), s>>>(nb, net->act[0], net->wf[0], net->p + net->boff[0], CO_REAL[0],
+  k_conv<16, 32, MODE_FWD><<<occ_grid(k_conv<16, 32, MODE_FWD>, conv_smem<16, 32>(), nb), NT, conv_smem<16, 32>(), s>>>(nb, net->act[0], net->wf[0], net->p + net->boff[0], CO_REAL[0],
                                                                  net->act[1], nullptr, none);
-  k_conv<32, 32, MODE_FWD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->act[1], net->wf[1], net->p + net->boff[1], CO_REAL[1],
+  k_conv<32, 32, MODE_FWD><<<occ_grid(k_conv<32, 32, MODE_FWD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->act[1], net->wf[1], net->p + net->boff[1], CO_REAL[1],
                                                                  net->act[2], nullptr, none);
-  k_conv<32, 32, MODE_FWD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->act[2], net->wf[2], net->p + net->boff[2], CO_REAL[2],
+  k_conv<32, 32, MODE_FWD><<<occ_grid(k_conv<32, 32, MODE_FWD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->act[2], net->wf[2], net->p + net->boff[2], CO_REAL[2],
                                                                  net->act[3], nullptr, none);
   count_launch(3);
   LossArgs la;
@@ -583,7 +592,7 @@ static bf_status net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, const f
   la.inv_m = b->N > 0 ? 1.0 / (double)b->N : 0.0;
   la.loss = mu_t ? net->loss : nullptr;
   if (mu_t) BF_CK(cudaMemsetAsync(net->loss, 0, sizeof(double), s));
-  k_conv<32, 16, MODE_LAST><<<grid, NT, conv_smem<32, 16>(), s>>>(nb, net->act[3], net->wf[3], net->p + net->boff[3], CO_REAL[3],
+  k_conv<32, 16, MODE_LAST><<<occ_grid(k_conv<32, 16, MODE_LAST>, conv_smem<32, 16>(), nb), NT, conv_smem<32, 16>(), s>>>(nb, net->act[3], net->wf[3], net->p + net->boff[3], CO_REAL[3],
                                                                 net->act[4], nullptr, la);
   count_launch();
   BF_CK(cudaGetLastError());
@@ -594,28 +603,27 @@ static bf_status net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, const f
 static bf_status net_backward(bf_ctx* ctx, bf_net* net, const bf_band* b) {
   cudaStream_t s = ctx->stream;
   const int nb = b->NB;
-  const int grid = nb < 152 ? nb : 152;
   for (int l = 0; l < 4; ++l) BF_CK(cudaMemsetAsync(net->gpad[l], 0, (size_t)27 * CI_PAD[l] * CO_PAD[l] * 4, s));
   BF_CK(cudaMemsetAsync(net->g, 0, net->P * 4, s));
   LossArgs none;
   memset(&none, 0, sizeof(none));
   // layer 4 (dy = act[4], written by the forward pass)
-  k_wgrad<32, 16><<<grid, NT, wgrad_smem<32, 16>(), s>>>(nb, net->act[3], net->act[4], net->gpad[3],
+  k_wgrad<32, 16><<<occ_grid(k_wgrad<32, 16>, wgrad_smem<32, 16>(), nb), NT, wgrad_smem<32, 16>(), s>>>(nb, net->act[3], net->act[4], net->gpad[3],
                                                          net->g + net->boff[3], CO_REAL[3]);
-  k_conv<16, 32, MODE_DGRAD><<<grid, NT, conv_smem<16, 32>(), s>>>(nb, net->act[4], net->wb[3], nullptr, 0,
+  k_conv<16, 32, MODE_DGRAD><<<occ_grid(k_conv<16, 32, MODE_DGRAD>, conv_smem<16, 32>(), nb), NT, conv_smem<16, 32>(), s>>>(nb, net->act[4], net->wb[3], nullptr, 0,
                                                                    net->gact[2], net->act[3], none);
   // layer 3
-  k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[2], net->gact[2], net->gpad[2],
+  k_wgrad<32, 32><<<occ_grid(k_wgrad<32, 32>, wgrad_smem<32, 32>(), nb), NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[2], net->gact[2], net->gpad[2],
                                                          net->g + net->boff[2], CO_REAL[2]);
-  k_conv<32, 32, MODE_DGRAD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->gact[2], net->wb[2], nullptr, 0,
+  k_conv<32, 32, MODE_DGRAD><<<occ_grid(k_conv<32, 32, MODE_DGRAD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->gact[2], net->wb[2], nullptr, 0,
                                                                    net->gact[1], net->act[2], none);
   // layer 2
-  k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->gact[1], net->gpad[1],
+  k_wgrad<32, 32><<<occ_grid(k_wgrad<32, 32>, wgrad_smem<32, 32>(), nb), NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->gact[1], net->gpad[1],
                                                          net->g + net->boff[1], CO_REAL[1]);
-  k_conv<32, 32, MODE_DGRAD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->gact[1], net->wb[1], nullptr, 0,
+  k_conv<32, 32, MODE_DGRAD><<<occ_grid(k_conv<32, 32, MODE_DGRAD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->gact[1], net->wb[1], nullptr, 0,
                                                                    net->gact[0], net->act[1], none);
   // layer 1
-  k_wgrad<16, 32><<<grid, NT, wgrad_smem<16, 32>(), s>>>(nb, net->act[0], net->gact[0], net->gpad[0],
+  k_wgrad<16, 32><<<occ_grid(k_wgrad<16, 32>, wgrad_smem<16, 32>(), nb), NT, wgrad_smem<16, 32>(), s>>>(nb, net->act[0], net->gact[0], net->gpad[0],
                                                          net->g + net->boff[0], CO_REAL[0]);
   count_launch(7);
   for (int l = 0; l < 4; ++l) {
@@ -829,7 +837,6 @@ bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* b, int which, in
   if (b->NB == 0) return BF_OK;
   cudaStream_t s = ctx->stream;
   const int nb = b->NB;
-  const int grid = nb < 152 ? nb : 152;
   // one forward with (arbitrary, finite) targets so that every buffer holds data
   BF_TRY(net_forward(ctx, net, b, b->tsdf, b->d, nullptr, nullptr));
   LossArgs none;
@@ -845,12 +852,12 @@ bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* b, int which, in
       BF_TRY(net_forward(ctx, net, b, b->tsdf, b->d, nullptr, nullptr));
       BF_TRY(net_backward(ctx, net, b));
     } else if (which == BF_NET_BENCH_CONV) {
-      k_conv<32, 32, MODE_FWD><<<grid, NT, conv_smem<32, 32>(), s>>>(nb, net->act[1], net->wf[1],
+      k_conv<32, 32, MODE_FWD><<<occ_grid(k_conv<32, 32, MODE_FWD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->act[1], net->wf[1],
                                                                      net->p + net->boff[1], CO_REAL[1], net->act[2],
                                                                      nullptr, none);
       count_launch();
     } else {
-      k_wgrad<32, 32><<<grid, NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->act[2], net->gpad[1],
+      k_wgrad<32, 32><<<occ_grid(k_wgrad<32, 32>, wgrad_smem<32, 32>(), nb), NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->act[2], net->gpad[1],
                                                              net->g + net->boff[1], CO_REAL[1]);
       count_launch();
     }

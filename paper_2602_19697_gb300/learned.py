@@ -78,3 +78,63 @@ def warm_solve(net: "bfsdf.Net", band: "bfsdf.Band", mu, rel_tol: float = 1e-6, 
     net.forward(band, mu, lsh)
     info = band.solve_mean(mu, rel_tol=rel_tol, fp64=fp64, warm=True)
     return info, lsh
+
+
+def surrogate_report(net: "bfsdf.Net", data: list[Example], K: int = 64, K_judge: int = 16, seed: int = 3) -> dict:
+    """Judge acceptance and probe iterations of the surrogate against the K-probe estimate, and the warm start's
+    relative residual, averaged over the examples."""
+    acc, it_s, it_f, r_net, r_tsdf, med = [], [], [], [], [], []
+    for ex in data:
+        b = ex.band
+        mh, lsh = torch.empty(b.N, device="cuda"), torch.empty(b.N, device="cuda")
+        net.forward(b, mh, lsh)
+        s = torch.empty(b.N, device="cuda")
+        info, _, _, na = b.surrogate_variance(lsh, s, K=K, K_judge=K_judge, seed=seed)
+        acc.append(na / max(b.NB, 1))
+        it_s.append(info.iters)
+        it_f.append(b.estimate_variance(torch.empty(b.N, device="cuda"), K=K, seed=seed).iters)
+        rel = (lsh.exp() - ex.s).abs() / torch.maximum(ex.s.abs(), torch.full_like(ex.s, 1e-30))
+        med.append(rel.median().item())
+        rhs = b.export_system()["rhs"].astype(np.float64)
+        for x, out in ((mh, r_net), (torch.from_numpy(b.export_band()["tsdf"] / np.float32(b.voxel)).cuda(), r_tsdf)):
+            y = torch.empty_like(x)
+            b.spmv(x.contiguous(), y)
+            out.append(float(np.linalg.norm(rhs - y.cpu().numpy()) / np.linalg.norm(rhs)))
+    return {"bricks_accepted": float(np.mean(acc)), "probe_iters_surrogate": float(np.mean(it_s)),
+            "probe_iters_full": float(np.mean(it_f)), "median_rel_err_s": float(np.mean(med)),
+            "warm_rel_residual": float(np.mean(r_net)), "tsdf_rel_residual": float(np.mean(r_tsdf))}
+
+
+def main(argv=None) -> None:
+    """Train on seeded sphere instances and report on held-out ones (one JSON line)."""
+    import argparse
+    import json
+    import time
+
+    import synth
+    from . import build
+
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--train", type=int, default=50)
+    ap.add_argument("--held-out", type=int, default=10)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args(argv)
+    build.build()
+    ctx = bfsdf.Context(0)
+    train_set = [make_example(ctx, synth.make_workload("sphere64", variant=i)) for i in range(a.train)]
+    held = [make_example(ctx, synth.make_workload("sphere64", variant=1000 + i)) for i in range(a.held_out)]
+    net = bfsdf.Net(ctx, seed=a.seed)
+    t0 = time.perf_counter()
+    hist = train(net, train_set, epochs=a.epochs, lr=a.lr)
+    torch.cuda.synchronize()
+    out = {"train_loss_first_epoch": hist[0], "train_loss_last_epoch": hist[-1],
+           "held_out_loss": evaluate(net, held), "train_seconds": time.perf_counter() - t0,
+           "steps": a.epochs * a.train}
+    out.update(surrogate_report(net, held))
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget (s)")
     ap.add_argument("--kernel", default=None,
-                    choices=["block_iter", "spmv", "net_forward", "net_train", "net_conv", "net_wgrad"],
+                    choices=["block_iter", "spmv", "net_forward", "net_train", "net_conv", "net_conv_mma", "net_wgrad"],
                     help="time one kernel alone on the workload's band (for profiling): --warmup untimed and "
                          "--steps timed launches; prints one JSON line with its throughput")
     return ap.parse_args()
@@ -378,9 +378,11 @@ def run_kernel(args):
     else:
         net = bfsdf.Net(ctx, seed=0)
         which = {"net_forward": bfsdf.BF_NET_BENCH_FORWARD, "net_train": bfsdf.BF_NET_BENCH_TRAIN,
-                 "net_conv": bfsdf.BF_NET_BENCH_CONV, "net_wgrad": bfsdf.BF_NET_BENCH_WGRAD}[args.kernel]
+                 "net_conv": bfsdf.BF_NET_BENCH_CONV, "net_wgrad": bfsdf.BF_NET_BENCH_WGRAD,
+                 "net_conv_mma": bfsdf.BF_NET_BENCH_CONV_MMA}[args.kernel]
         flops = {"net_forward": bfsdf.NET_FLOPS_FWD, "net_train": 3 * bfsdf.NET_FLOPS_FWD - 2 * 1000 * 27 * 2 * 32,
-                 "net_conv": bfsdf.NET_FLOPS_CONV, "net_wgrad": bfsdf.NET_FLOPS_CONV}[args.kernel] * NB
+                 "net_conv": bfsdf.NET_FLOPS_CONV, "net_wgrad": bfsdf.NET_FLOPS_CONV,
+                 "net_conv_mma": bfsdf.NET_FLOPS_CONV}[args.kernel] * NB
         net.bench(band, which, reps=max(args.warmup, 1))
         ms = net.bench(band, which, reps=max(args.steps, 1))
         out.update(ms_per_rep=ms, flops_per_rep=flops, achieved_tflops=flops / (ms * 1e-3) / 1e12)

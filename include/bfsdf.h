@@ -287,13 +287,15 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* band, const float* log_s_h
  * context stream, mean ms per repetition over `reps`):
  *   BF_NET_BENCH_FORWARD: bf_net_forward's kernels (features + 4 convolutions);
  *   BF_NET_BENCH_TRAIN: forward with loss + backward (no Adam step);
- *   BF_NET_BENCH_CONV: one 32 -> 32 forward convolution (layer 2);
- *   BF_NET_BENCH_WGRAD: one 32 x 32 weight-gradient pass (layer 2).
+ *   BF_NET_BENCH_CONV: one 32 -> 32 forward convolution (layer 2; tcgen05 kernel);
+ *   BF_NET_BENCH_WGRAD: one 32 x 32 weight-gradient pass (layer 2);
+ *   BF_NET_BENCH_CONV_MMA: the same convolution on the mma.sync kernel.
  * Activations and gradients of the network are overwritten. */
 #define BF_NET_BENCH_FORWARD 0
 #define BF_NET_BENCH_TRAIN 1
 #define BF_NET_BENCH_CONV 2
 #define BF_NET_BENCH_WGRAD 3
+#define BF_NET_BENCH_CONV_MMA 4
 bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* band, int which, int reps, double* ms_per_rep);
 
 /* Kernel timing for roofline measurements: launches kernels of the solver

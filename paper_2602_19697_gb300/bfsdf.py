@@ -37,7 +37,7 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_net_bench"]
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
-BF_NET_BENCH_FORWARD, BF_NET_BENCH_TRAIN, BF_NET_BENCH_CONV, BF_NET_BENCH_WGRAD = range(4)
+BF_NET_BENCH_FORWARD, BF_NET_BENCH_TRAIN, BF_NET_BENCH_CONV, BF_NET_BENCH_WGRAD, BF_NET_BENCH_CONV_MMA = range(5)
 # algorithmic FLOPs of the network per brick tile (10^3 voxels, 27 taps, real channels)
 NET_FLOPS_FWD = 2 * 1000 * 27 * (2 * 32 + 32 * 32 + 32 * 32 + 32 * 2)
 NET_FLOPS_CONV = 2 * 1000 * 27 * 32 * 32

@@ -236,6 +236,263 @@ __global__ void __launch_bounds__(NT, 1) k_conv(int nb, const __nv_bfloat16* __r
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core (tcgen05) form of the same convolution.
+//
+// One CTA per SM walks the bricks.  The input tile lives in shared memory in
+// the canonical K-major, no-swizzle operand layout: plane c (channels
+// 8c .. 8c+7) holds one 16-byte row per padded voxel row p (12^3 tile with a
+// zero border, rows up to TC_ROWS), so the A operand of tap t for output rows
+// p0 .. p0+127 is the 128 rows starting at p0 + off(t): an 8-row core matrix
+// is 128 contiguous bytes (stride between core matrices along M: 128 B; along
+// K: one plane).  The weights are staged once, per tap and 8-channel chunk a
+// [C_out][8] block (the B operand, K-major).  Output rows cover the interior
+// rows [157, 157 + 12 x 128); each 128-row M tile accumulates in its own TMEM
+// columns (D: 128 lanes x C_out FP32), over 27 taps x C_in/16 MMAs of
+// M128 x N(C_out) x K16, issued by two threads (six tiles each), completed
+// through an mbarrier; the next brick's input is read into registers while
+// the MMAs run.
+// The epilogue (bias, ReLU / loss / ReLU mask) reads TMEM with tcgen05.ld and
+// writes the interior rows.
+constexpr int TC_P0 = 157;                 // first interior padded row
+constexpr int TC_MT = 12;                  // 128-row M tiles per brick
+constexpr int TC_ROWS = 1856;              // padded rows held (>= 157 + 1536 + 157)
+constexpr int TC_NT = 256;                 // threads per CTA (two warpgroups)
+static_assert(TC_P0 + 128 * TC_MT + 157 <= TC_ROWS, "tile rows");
+
+template <int CIN, int COUT>
+__host__ __device__ constexpr size_t tc_smem() {
+  return (size_t)TC_ROWS * CIN * 2 + (size_t)27 * CIN * COUT * 2 + COUT * 4 + 64;
+}
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  // shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+  // offsets in 16-byte units, descriptor version 1, no swizzle
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+template <int N>
+__host__ __device__ constexpr uint32_t tc_idesc() {
+  // kind::f16 instruction descriptor: D FP32, A and B bf16, both K-major, N, M = 128
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool tc_wait(uint64_t* mbar, uint32_t parity) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(mbar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// 32 lanes x 16 consecutive 32-bit TMEM columns into 16 registers per thread
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(TC_NT, 1) k_conv_tc(int nb, const __nv_bfloat16* __restrict__ x,
+                                                      const __nv_bfloat16* __restrict__ w,
+                                                      const float* __restrict__ bias, int nbias,
+                                                      __nv_bfloat16* __restrict__ y,
+                                                      const __nv_bfloat16* __restrict__ mask, LossArgs la,
+                                                      int* __restrict__ err) {
+  extern __shared__ __align__(16) uint8_t tsm[];
+  constexpr int NPL = CIN / 8;  // 8-channel planes of the input tile
+  constexpr int KS = CIN / 16;  // K16 steps per tap
+  constexpr uint32_t TCOLS = COUT * TC_MT > 256 ? 512 : 256;
+  __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(tsm);  // [NPL][TC_ROWS][8]
+  __nv_bfloat16* wsm = act + (size_t)TC_ROWS * CIN;              // [27][NPL][COUT][8]
+  float* bs = reinterpret_cast<float*>(wsm + (size_t)27 * CIN * COUT);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(bs + COUT);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // zero tile (the border rows stay zero), weights in operand order, bias
+  for (int q = tid; q < TC_ROWS * CIN / 8; q += TC_NT) reinterpret_cast<uint4*>(act)[q] = make_uint4(0, 0, 0, 0);
+  for (int q = tid; q < 27 * COUT * NPL; q += TC_NT) {  // q: global 16-byte chunk of w[27][COUT][CIN]
+    const int tap = q / (COUT * NPL), rem = q - tap * COUT * NPL, co = rem / NPL, c = rem - co * NPL;
+    reinterpret_cast<uint4*>(wsm)[(tap * NPL + c) * COUT + co] = reinterpret_cast<const uint4*>(w)[q];
+  }
+  for (int q = tid; q < COUT; q += TC_NT) bs[q] = (bias && q < nbias) ? bias[q] : 0.0f;
+  if (tid == 0) {
+    // two arrivals per phase: the commits of the two issuing threads
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"((uint32_t)__cvta_generic_to_shared(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(tslot)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t act_s = (uint32_t)__cvta_generic_to_shared(act), w_s = (uint32_t)__cvta_generic_to_shared(wsm);
+  double lsum = 0.0;
+  // the next brick's input is loaded into registers while the tensor cores work on the current one
+  constexpr int PER = (TV * NPL + TC_NT - 1) / TC_NT;  // 16-byte chunks per thread and brick
+  uint4 pre[PER];
+  auto load_brick = [&](int bb) {
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int q = tid + i * TC_NT;
+      if (bb < nb && q < TV * NPL)
+        pre[i] = __ldg(reinterpret_cast<const uint4*>(x + (size_t)bb * TV * CIN) + q);  // chunk q = (v, c)
+    }
+  };
+  load_brick(blockIdx.x);
+  const uint64_t ad0 = tc_desc(act_s, TC_ROWS * 16u, 128u), bd0 = tc_desc(w_s, COUT * 16u, 128u);
+  int it = 0;
+  for (int b = blockIdx.x; b < nb; b += gridDim.x, ++it) {
+    // the brick's 1000 rows into the interior of the tile (the previous MMAs have read the tile)
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+      const int q = tid + i * TC_NT;
+      if (q < TV * NPL) {
+        const int v = q / NPL, c = q - v * NPL;
+        reinterpret_cast<uint4*>(act)[(size_t)c * TC_ROWS + prow(v)] = pre[i];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((tid & 127) == 0) {  // two issuing threads, six M tiles each; descriptors advance by 16-byte units
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int m0 = (tid >> 7) * (TC_MT / 2);
+      for (int mt = m0; mt < m0 + TC_MT / 2; ++mt) {
+        const int p0 = TC_P0 + 128 * mt;
+        for (int tap = 0; tap < 27; ++tap) {
+          const uint64_t ar = ad0 + (uint64_t)(p0 + tap_off(tap));
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks)
+            tc_mma(tmem + (uint32_t)(mt * COUT), ar + (uint64_t)(2 * ks * TC_ROWS),
+                   bd0 + (uint64_t)((tap * NPL + 2 * ks) * COUT), tc_idesc<COUT>(), (tap | ks) != 0);
+        }
+      }
+      tc_commit(mbar);
+    }
+    load_brick(b + gridDim.x);
+    const bool ok = tc_wait(mbar, (uint32_t)it & 1u);
+    if (__syncthreads_or(!ok)) {  // the MMAs did not complete in time: report and stop
+      if (tid == 0) atomicExch(err, 1);
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warpgroup g takes M tiles g, g + 2, ...; warp w reads TMEM lanes 32 (w % 4) ..
+    const int lq = warp & 3;
+    for (int mt = warp >> 2; mt < TC_MT; mt += 2) {
+      const int p = TC_P0 + 128 * mt + 32 * lq + lane;
+      const uint32_t taddr = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(mt * COUT);
+      float acc[COUT];
+#pragma unroll
+      for (int k0 = 0; k0 < COUT; k0 += 16) {
+        float t[16];
+        tc_ld16(taddr + (uint32_t)k0, t);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k0 + k] = t[k];
+      }
+      const int px = p % 12, py = (p / 12) % 12, pz = p / 144;
+      if (px < 1 || px > 10 || py < 1 || py > 10 || pz < 1 || pz > 10) continue;
+      const int v = (px - 1) + 10 * (py - 1) + 100 * (pz - 1);
+      const size_t o = ((size_t)b * TV + v) * COUT;
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) acc[co] += bs[co];
+      if (MODE == MODE_FWD) {
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = fmaxf(acc[co], 0.0f);
+      } else if (MODE == MODE_DGRAD) {
+#pragma unroll
+        for (int c8 = 0; c8 < COUT / 8; ++c8) {
+          const uint4 m4 = reinterpret_cast<const uint4*>(mask + o)[c8];
+          const __nv_bfloat16* mv = reinterpret_cast<const __nv_bfloat16*>(&m4);
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (!(__bfloat162float(mv[k]) > 0.0f)) acc[8 * c8 + k] = 0.0f;
+        }
+      } else {  // MODE_LAST: channels 0, 1 are (o0, o1) -> predictions, loss, dL/do
+        float d0 = 0.0f, d1 = 0.0f;
+        const int tx = v % 10, ty = (v / 10) % 10, tz = v / 100;
+        if (tx >= 1 && tx <= 8 && ty >= 1 && ty <= 8 && tz >= 1 && tz <= 8) {
+          const int l = (tx - 1) + 8 * (ty - 1) + 64 * (tz - 1);
+          const MetaWord m = la.B.meta[16 * b + (l >> 5)];
+          const uint32_t bit = 1u << (l & 31);
+          if (m.bits & bit) {
+            const int idx = m.base + __popc(m.bits & (bit - 1u));
+            const float mh = la.tsdf[idx] / la.B.h + acc[0];
+            const float lh = (float)((double)acc[1] - log((double)la.qd[idx]));
+            if (la.mu_hat) {
+              la.mu_hat[idx] = mh;
+              la.ls_hat[idx] = lh;
+            }
+            if (la.mu_t) {
+              const double st = fmax((double)la.s_t[idx], 1.0 / (double)la.qd[idx]);
+              const double e0 = (double)mh - (double)la.mu_t[idx], e1 = (double)lh - log(st);
+              lsum += (e0 * e0 + e1 * e1) * la.inv_m;
+              d0 = (float)(2.0 * e0 * la.inv_m);
+              d1 = (float)(2.0 * e1 * la.inv_m);
+            }
+          }
+        }
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = 0.0f;
+        acc[0] = d0;
+        acc[1] = d1;
+      }
+#pragma unroll
+      for (int c8 = 0; c8 < COUT / 8; ++c8) {
+        uint4 o4;
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o4);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(acc[8 * c8 + 2 * k], acc[8 * c8 + 2 * k + 1]);
+        reinterpret_cast<uint4*>(y + o)[c8] = o4;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // TMEM reads and tile reads of this brick are done
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+  if (MODE == MODE_LAST && la.loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && lsum != 0.0) atomicAdd(la.loss, lsum);
+  }
+}
+
 // Weight and bias gradients: dW[tap][ci][co] += sum_v x[v + tap][ci] dy[v][co],
 // db[co] += sum_v dy[v][co] (co < nbias), over the CTA's bricks, added into fp32 dW, db.
 // Warp w owns taps w, w + 8, w + 16, w + 24; a k-step is 16 output voxels.
@@ -499,6 +756,7 @@ struct bf_net {
   __nv_bfloat16* gact[3] = {nullptr, nullptr, nullptr};                   // dz1, dz2, dz3
   double* loss = nullptr;
   double* h_loss = nullptr;
+  int* err = nullptr;  // set by a tensor-core kernel whose MMAs did not complete in time
   bool attr = false;
 };
 
@@ -528,8 +786,33 @@ static int occ_grid(K kern, size_t smem, int nb) {
   return nb < g ? nb : g;
 }
 
+template <int CIN, int COUT>
+constexpr int tc_launch_smem() {  // at least 120 KB, so that one CTA (and one TMEM allocation) fits per SM
+  return tc_smem<CIN, COUT>() > 120 * 1024 ? (int)tc_smem<CIN, COUT>() : 120 * 1024;
+}
+
+// tensor-core convolution over the band's bricks (one CTA per SM)
+template <int CIN, int COUT, int MODE>
+static void conv_tc(cudaStream_t s, bf_net* net, int nb, const __nv_bfloat16* x, const __nv_bfloat16* w,
+                    const float* bias, int nbias, __nv_bfloat16* y, const __nv_bfloat16* mask, const LossArgs& la) {
+  const int grid = nb < 152 ? nb : 152;
+  k_conv_tc<CIN, COUT, MODE><<<grid, TC_NT, tc_launch_smem<CIN, COUT>(), s>>>(nb, x, w, bias, nbias, y, mask, la,
+                                                                              net->err);
+  count_launch();
+}
+
 static bf_status set_attrs(bf_ctx* ctx, bf_net* net) {
   if (net->attr) return BF_OK;
+  BF_CK(cudaFuncSetAttribute(k_conv_tc<16, 32, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_launch_smem<16, 32>()));
+  BF_CK(cudaFuncSetAttribute(k_conv_tc<32, 32, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_launch_smem<32, 32>()));
+  BF_CK(cudaFuncSetAttribute(k_conv_tc<32, 16, MODE_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_launch_smem<32, 16>()));
+  BF_CK(cudaFuncSetAttribute(k_conv_tc<16, 32, MODE_DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_launch_smem<16, 32>()));
+  BF_CK(cudaFuncSetAttribute(k_conv_tc<32, 32, MODE_DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc_launch_smem<32, 32>()));
   BF_CK(cudaFuncSetAttribute(k_conv<16, 32, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)conv_smem<16, 32>()));
   BF_CK(cudaFuncSetAttribute(k_conv<32, 32, MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -574,13 +857,12 @@ static bf_status net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, const f
   count_launch();
   LossArgs none;
   memset(&none, 0, sizeof(none));
-  k_conv<16, 32, MODE_FWD><<<occ_grid(k_conv<16, 32, MODE_FWD>, conv_smem<16, 32>(), nb), NT, conv_smem<16, 32>(), s>>>(nb, net->act[0], net->wf[0], net->p + net->boff[0], CO_REAL[0],
-                                                                 net->act[1], nullptr, none);
-  k_conv<32, 32, MODE_FWD><<<occ_grid(k_conv<32, 32, MODE_FWD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->act[1], net->wf[1], net->p + net->boff[1], CO_REAL[1],
-                                                                 net->act[2], nullptr, none);
-  k_conv<32, 32, MODE_FWD><<<occ_grid(k_conv<32, 32, MODE_FWD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->act[2], net->wf[2], net->p + net->boff[2], CO_REAL[2],
-                                                                 net->act[3], nullptr, none);
-  count_launch(3);
+  conv_tc<16, 32, MODE_FWD>(s, net, nb, net->act[0], net->wf[0], net->p + net->boff[0], CO_REAL[0], net->act[1],
+                            nullptr, none);
+  conv_tc<32, 32, MODE_FWD>(s, net, nb, net->act[1], net->wf[1], net->p + net->boff[1], CO_REAL[1], net->act[2],
+                            nullptr, none);
+  conv_tc<32, 32, MODE_FWD>(s, net, nb, net->act[2], net->wf[2], net->p + net->boff[2], CO_REAL[2], net->act[3],
+                            nullptr, none);
   LossArgs la;
   la.B = bv;
   la.tsdf = b->tsdf;
@@ -592,9 +874,8 @@ static bf_status net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, const f
   la.inv_m = b->N > 0 ? 1.0 / (double)b->N : 0.0;
   la.loss = mu_t ? net->loss : nullptr;
   if (mu_t) BF_CK(cudaMemsetAsync(net->loss, 0, sizeof(double), s));
-  k_conv<32, 16, MODE_LAST><<<occ_grid(k_conv<32, 16, MODE_LAST>, conv_smem<32, 16>(), nb), NT, conv_smem<32, 16>(), s>>>(nb, net->act[3], net->wf[3], net->p + net->boff[3], CO_REAL[3],
-                                                                net->act[4], nullptr, la);
-  count_launch();
+  conv_tc<32, 16, MODE_LAST>(s, net, nb, net->act[3], net->wf[3], net->p + net->boff[3], CO_REAL[3], net->act[4],
+                             nullptr, la);
   BF_CK(cudaGetLastError());
   return BF_OK;
 }
@@ -610,28 +891,38 @@ static bf_status net_backward(bf_ctx* ctx, bf_net* net, const bf_band* b) {
   // layer 4 (dy = act[4], written by the forward pass)
   k_wgrad<32, 16><<<occ_grid(k_wgrad<32, 16>, wgrad_smem<32, 16>(), nb), NT, wgrad_smem<32, 16>(), s>>>(nb, net->act[3], net->act[4], net->gpad[3],
                                                          net->g + net->boff[3], CO_REAL[3]);
-  k_conv<16, 32, MODE_DGRAD><<<occ_grid(k_conv<16, 32, MODE_DGRAD>, conv_smem<16, 32>(), nb), NT, conv_smem<16, 32>(), s>>>(nb, net->act[4], net->wb[3], nullptr, 0,
-                                                                   net->gact[2], net->act[3], none);
+  conv_tc<16, 32, MODE_DGRAD>(s, net, nb, net->act[4], net->wb[3], nullptr, 0, net->gact[2], net->act[3], none);
   // layer 3
   k_wgrad<32, 32><<<occ_grid(k_wgrad<32, 32>, wgrad_smem<32, 32>(), nb), NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[2], net->gact[2], net->gpad[2],
                                                          net->g + net->boff[2], CO_REAL[2]);
-  k_conv<32, 32, MODE_DGRAD><<<occ_grid(k_conv<32, 32, MODE_DGRAD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->gact[2], net->wb[2], nullptr, 0,
-                                                                   net->gact[1], net->act[2], none);
+  conv_tc<32, 32, MODE_DGRAD>(s, net, nb, net->gact[2], net->wb[2], nullptr, 0, net->gact[1], net->act[2], none);
   // layer 2
   k_wgrad<32, 32><<<occ_grid(k_wgrad<32, 32>, wgrad_smem<32, 32>(), nb), NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->gact[1], net->gpad[1],
                                                          net->g + net->boff[1], CO_REAL[1]);
-  k_conv<32, 32, MODE_DGRAD><<<occ_grid(k_conv<32, 32, MODE_DGRAD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->gact[1], net->wb[1], nullptr, 0,
-                                                                   net->gact[0], net->act[1], none);
+  conv_tc<32, 32, MODE_DGRAD>(s, net, nb, net->gact[1], net->wb[1], nullptr, 0, net->gact[0], net->act[1], none);
   // layer 1
   k_wgrad<16, 32><<<occ_grid(k_wgrad<16, 32>, wgrad_smem<16, 32>(), nb), NT, wgrad_smem<16, 32>(), s>>>(nb, net->act[0], net->gact[0], net->gpad[0],
                                                          net->g + net->boff[0], CO_REAL[0]);
-  count_launch(7);
+  count_launch(4);  // the weight-gradient launches (conv_tc counts its own)
   for (int l = 0; l < 4; ++l) {
     k_unpad_grad<<<gs(27 * CI_REAL[l] * CO_REAL[l]), 256, 0, s>>>(net->gpad[l], CI_REAL[l], CO_REAL[l], CI_PAD[l],
                                                                  CO_PAD[l], net->g + net->woff[l]);
     count_launch();
   }
   BF_CK(cudaGetLastError());
+  return BF_OK;
+}
+
+// synchronise and report a tensor-core kernel whose MMAs did not complete in time
+static bf_status net_sync_check(bf_ctx* ctx, bf_net* net) {
+  int* h_err = reinterpret_cast<int*>(net->h_loss + 1);
+  BF_CK(cudaMemcpyAsync(h_err, net->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  BF_CK(cudaStreamSynchronize(ctx->stream));
+  if (*h_err) {
+    *h_err = 0;
+    cudaMemsetAsync(net->err, 0, sizeof(int), ctx->stream);
+    return bf_fail(ctx, BF_ECUDA, "network: tensor-core MMAs did not complete in time");
+  }
   return BF_OK;
 }
 
@@ -655,8 +946,8 @@ bf_status bf_net_create(bf_ctx* ctx, uint64_t seed, bf_net** out) {
     return st;
   };
   if (cudaMalloc(&net->p, net->P * 4) || cudaMalloc(&net->g, net->P * 4) || cudaMalloc(&net->m, net->P * 4) ||
-      cudaMalloc(&net->v, net->P * 4) || cudaMalloc(&net->loss, sizeof(double)) ||
-      cudaMallocHost(&net->h_loss, sizeof(double)))
+      cudaMalloc(&net->v, net->P * 4) || cudaMalloc(&net->loss, sizeof(double)) || cudaMalloc(&net->err, sizeof(int)) ||
+      cudaMallocHost(&net->h_loss, 2 * sizeof(double)))
     return fail(bf_fail(ctx, BF_ENOMEM, "bf_net_create: allocation failed"));
   for (int l = 0; l < 4; ++l) {
     const size_t nw = (size_t)27 * CI_PAD[l] * CO_PAD[l];
@@ -669,6 +960,7 @@ bf_status bf_net_create(bf_ctx* ctx, uint64_t seed, bf_net** out) {
   count_launch();
   cudaMemsetAsync(net->m, 0, net->P * 4, s);
   cudaMemsetAsync(net->v, 0, net->P * 4, s);
+  cudaMemsetAsync(net->err, 0, sizeof(int), s);
   bf_status st = net_pack(ctx, net);
   if (st) return fail(st);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(bf_fail(ctx, BF_ECUDA, "bf_net_create"));
@@ -679,7 +971,7 @@ bf_status bf_net_create(bf_ctx* ctx, uint64_t seed, bf_net** out) {
 void bf_net_destroy(bf_net* net) {
   if (!net) return;
   cudaDeviceSynchronize();
-  void* ptrs[] = {net->p, net->g, net->m, net->v, net->loss};
+  void* ptrs[] = {net->p, net->g, net->m, net->v, net->loss, net->err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (net->h_loss) cudaFreeHost(net->h_loss);
@@ -722,6 +1014,7 @@ bf_status bf_net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, float* mu_h
   BF_TRY(stage_out(ctx, mu_hat, b->N, WS_OUT0, &dm, &hm));
   BF_TRY(stage_out(ctx, log_s_hat, b->N, WS_OUT1, &dl, &hl));
   BF_TRY(net_forward(ctx, net, b, nullptr, nullptr, dm, dl));
+  BF_TRY(net_sync_check(ctx, net));
   BF_TRY(copy_out(ctx, mu_hat, (const float*)dm, b->N, hm));
   BF_TRY(copy_out(ctx, log_s_hat, (const float*)dl, b->N, hl));
   return BF_OK;
@@ -753,7 +1046,7 @@ bf_status bf_net_train_step(bf_ctx* ctx, bf_net* net, const bf_band* b, const fl
     BF_TRY(net_pack(ctx, net));
   }
   BF_CK(cudaMemcpyAsync(net->h_loss, net->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
-  BF_CK(cudaStreamSynchronize(s));
+  BF_TRY(net_sync_check(ctx, net));
   if (loss) *loss = *net->h_loss;
   return BF_OK;
 }
@@ -831,7 +1124,7 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
 }
 
 bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* b, int which, int reps, double* ms) {
-  if (!ctx || !net || !b || !ms || reps < 1 || which < 0 || which > 3) return BF_EINVAL;
+  if (!ctx || !net || !b || !ms || reps < 1 || which < 0 || which > 4) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_net_bench: call bf_integrate_depth first");
   *ms = 0.0;
   if (b->NB == 0) return BF_OK;
@@ -852,9 +1145,12 @@ bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* b, int which, in
       BF_TRY(net_forward(ctx, net, b, b->tsdf, b->d, nullptr, nullptr));
       BF_TRY(net_backward(ctx, net, b));
     } else if (which == BF_NET_BENCH_CONV) {
-      k_conv<32, 32, MODE_FWD><<<occ_grid(k_conv<32, 32, MODE_FWD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(), s>>>(nb, net->act[1], net->wf[1],
-                                                                     net->p + net->boff[1], CO_REAL[1], net->act[2],
-                                                                     nullptr, none);
+      conv_tc<32, 32, MODE_FWD>(s, net, nb, net->act[1], net->wf[1], net->p + net->boff[1], CO_REAL[1], net->act[2],
+                                nullptr, none);
+    } else if (which == BF_NET_BENCH_CONV_MMA) {
+      k_conv<32, 32, MODE_FWD><<<occ_grid(k_conv<32, 32, MODE_FWD>, conv_smem<32, 32>(), nb), NT, conv_smem<32, 32>(),
+                                 s>>>(nb, net->act[1], net->wf[1], net->p + net->boff[1], CO_REAL[1], net->act[2],
+                                      nullptr, none);
       count_launch();
     } else {
       k_wgrad<32, 32><<<occ_grid(k_wgrad<32, 32>, wgrad_smem<32, 32>(), nb), NT, wgrad_smem<32, 32>(), s>>>(nb, net->act[1], net->act[2], net->gpad[1],
@@ -869,7 +1165,7 @@ bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* b, int which, in
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *ms = t / reps;
-  return BF_OK;
+  return net_sync_check(ctx, net);
 }
 
 }  // extern "C"

@@ -156,35 +156,74 @@ __device__ __forceinline__ T nsum(const T* t, int c) {
   return ((t[c - 1] + t[c + 1]) + (t[c - 10] + t[c + 10])) + (t[c - 100] + t[c + 100]);
 }
 
-// y = Q x (plain SpMV, FP32)
-__global__ void __launch_bounds__(BT) k_spmv(BandView B, float lam, const float* __restrict__ qd,
-                                             const float* __restrict__ x, float* __restrict__ y) {
+// Halo slots of a face f = 2 axis + side (side 0: the -axis neighbour's
+// layer 7, side 1: the +axis neighbour's layer 0), at face coordinates (u, v)
+// along the two other axes in increasing order: local index in the neighbour
+// brick = [0] + u [1] + v [2], position in the 10^3 tile = [3] + u [4] + v [5]
+// (the same mapping as halo_slot).
+__constant__ int c_halo[6][6] = {
+    {7, 8, 64, 10 + 100, 10, 100},       {0, 8, 64, 9 + 10 + 100, 10, 100},
+    {56, 1, 64, 1 + 100, 1, 100},        {0, 1, 64, 1 + 90 + 100, 1, 100},
+    {448, 1, 8, 1 + 10, 1, 10},          {0, 1, 8, 1 + 10 + 900, 1, 10},
+};
+
+// y = Q x (plain SpMV, FP32).  A CTA walks bricks b, b + grid, ...; the
+// lookup words of the next brick and its six neighbours are fetched into
+// registers while the current brick's x is gathered, and the neighbour ranks
+// one brick further ahead, so a brick costs one round trip to memory.
+constexpr int SPMV_OCC = 12;  // resident CTAs per SM (40 registers x 128 threads)
+
+// rank of brick b (thread's slot 0) or of its face neighbour (slots 1-6); -1 if none
+__device__ __forceinline__ int meta_rank(const BandView& B, int b) {
+  const int which = threadIdx.x >> 4;
+  if (b >= B.NB || threadIdx.x >= 7 * 16) return -1;
+  return which == 0 ? b : __ldg(B.nbr + 6 * b + which - 1);
+}
+__device__ __forceinline__ MetaWord meta_word(const BandView& B, int r) {
+  MetaWord m;
+  m.bits = 0;
+  m.base = 0;
+  if (r >= 0) m = B.meta[16 * r + (threadIdx.x & 15)];
+  return m;
+}
+
+__global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, const float* __restrict__ qd,
+                                                       const float* __restrict__ x, float* __restrict__ y) {
   __shared__ float tile[1000];
   __shared__ MetaWord sm[7][16];
+  MetaWord nm = meta_word(B, meta_rank(B, blockIdx.x));
+  int nr = meta_rank(B, blockIdx.x + gridDim.x);
   for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
+    __syncthreads();  // the previous brick's readers of tile and sm are done
+    if (threadIdx.x < 7 * 16) sm[threadIdx.x >> 4][threadIdx.x & 15] = nm;
     __syncthreads();
-    load_meta(B, b, sm);
-    __syncthreads();
+    nm = meta_word(B, nr);                   // next brick (its rank arrived during the previous brick)
+    nr = meta_rank(B, b + 2 * gridDim.x);    // the brick after
+    // own voxels: thread t takes local indices 4t .. 4t+3 (one lookup word, one x-row of the tile)
+    const int l0 = 4 * threadIdx.x;
+    const MetaWord m = sm[0][l0 >> 5];
+    const uint32_t bits = m.bits >> (l0 & 31);
+    int i = m.base + __popc(m.bits & ((1u << (l0 & 31)) - 1u));
+    const int c0 = own_tile(l0);
     int idx[4];
+    float q[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      int l = threadIdx.x + BT * s;
-      idx[s] = slot_index(sm, 0, l);
-      tile[own_tile(l)] = idx[s] >= 0 ? __ldg(x + idx[s]) : 0.0f;
+      idx[s] = ((bits >> s) & 1u) ? i++ : -1;
+      tile[c0 + s] = idx[s] >= 0 ? __ldg(x + idx[s]) : 0.0f;
+      q[s] = idx[s] >= 0 ? __ldg(qd + idx[s]) : 0.0f;
     }
+    // halo: slot h = face f (warp-uniform), face coordinates (u, v)
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      int j, tp;
-      halo_slot(sm, threadIdx.x + BT * s, &j, &tp);
-      tile[tp] = j >= 0 ? __ldg(x + j) : 0.0f;
+      const int h = threadIdx.x + BT * s, f = h >> 6, u = h & 7, v = (h >> 3) & 7;
+      const int j = slot_index(sm, 1 + f, c_halo[f][0] + u * c_halo[f][1] + v * c_halo[f][2]);
+      tile[c_halo[f][3] + u * c_halo[f][4] + v * c_halo[f][5]] = j >= 0 ? __ldg(x + j) : 0.0f;
     }
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      if (idx[s] < 0) continue;
-      int c = own_tile(threadIdx.x + BT * s);
-      y[idx[s]] = __ldg(qd + idx[s]) * tile[c] - lam * nsum(tile, c);
-    }
+    for (int s = 0; s < 4; ++s)
+      if (idx[s] >= 0) y[idx[s]] = q[s] * tile[c0 + s] - lam * nsum(tile, c0 + s);
   }
 }
 
@@ -624,7 +663,7 @@ bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, uns
 
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   if (b->N == 0) return BF_OK;
-  const int grid = b->NB < NCTA ? b->NB : NCTA;
+  const int grid = b->NB < 152 * SPMV_OCC ? b->NB : 152 * SPMV_OCC;
   k_spmv<<<grid, BT, 0, ctx->stream>>>(band_view(b), (float)b->prm.lambda, b->qd, x, y);
   count_launch();
   BF_CK(cudaGetLastError());

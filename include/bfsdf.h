@@ -233,7 +233,7 @@ bf_status bf_solve_mean_static(bf_ctx* ctx, bf_band* band, double rel_tol, int m
  *   Parameters: one float vector of bf_net_nparams() = 58,850 values,
  *   W1 b1 W2 b2 W3 b3 W4 b4 with W_l[tap][ci][co], tap = 9 (dz+1) + 3 (dy+1)
  *   + (dx+1), b_l[co].  The library keeps an FP32 master copy and Adam
- *   moments; the convolutions run on bf16 tensor-core operands with FP32
+ *   moments; the convolutions run on bf16 tensor-core operands (tcgen05) with FP32
  *   accumulation.
  *   Loss over the band voxels j (M of them):
  *   L = (1/M) sum_j (mu_hat_j - mu_j)^2 + (log s_hat_j - log max(s_j, 1/Q_jj))^2. */

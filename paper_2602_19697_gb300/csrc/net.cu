@@ -10,14 +10,15 @@
 // on the TSDF and on the Jacobi lower bound 1/Q_ii of (Q^-1)_ii); loss = mean
 // over band voxels of (mu_hat - mu)^2 + (log s_hat - log max(s, 1/Q_ii))^2.
 //
-// Kernels: implicit GEMM on tensor cores (bf16 x bf16 -> fp32, mma.sync
-// m16n8k16 with ldmatrix operand loads).  A CTA stages one brick tile at a
-// time in shared memory with a zero border (12^3 rows of C channels), so a
-// tap shift is a row offset; warps take 16-voxel output tiles.
-//   k_conv<FWD>      y = relu(conv(x) + b)                 (layers 1-3)
-//   k_conv<LAST>     o = conv(x) + b; predictions; loss and dL/do at band voxels
-//   k_conv<DGRAD>    dx = conv(dy, W flipped and transposed) * [x_prev > 0]
-//   k_wgrad          dW[tap][ci][co] += sum_v x[v + tap][ci] dy[v][co], db
+// Kernels: implicit GEMM on tensor cores (bf16 x bf16 -> fp32).  A CTA stages
+// one brick tile at a time in shared memory with a zero border (12^3 rows of
+// C channels), so a tap shift is a row offset.
+//   k_conv_tc<FWD>   y = relu(conv(x) + b)                 (layers 1-3; tcgen05, TMEM)
+//   k_conv_tc<LAST>  o = conv(x) + b; predictions; loss and dL/do at band voxels
+//   k_conv_tc<DGRAD> dx = conv(dy, W flipped and transposed) * [x_prev > 0]
+//   k_wgrad          dW[tap][ci][co] += sum_v x[v + tap][ci] dy[v][co], db (mma.sync)
+//   k_conv           the same convolutions on mma.sync m16n8k16 with ldmatrix
+//                    operand loads (16-voxel output tiles per warp); timing only
 // Weights: FP32 master copy (oracle layout W[tap][ci][co], b[co]) with Adam
 // moments; bf16 copies packed as [tap][co][ci] (forward) and
 // [tap'][ci][co] with tap' = 26 - tap (backward data).

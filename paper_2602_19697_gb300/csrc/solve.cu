@@ -172,6 +172,7 @@ __constant__ int c_halo[6][6] = {
 // registers while the current brick's x is gathered, and the neighbour ranks
 // one brick further ahead, so a brick costs one round trip to memory.
 constexpr int SPMV_OCC = 12;  // resident CTAs per SM (40 registers x 128 threads)
+constexpr int CG_OCC = 8, CG_NCTA = 152 * CG_OCC;  // k_cg: resident CTAs per SM, grid
 
 // rank of brick b (thread's slot 0) or of its face neighbour (slots 1-6); -1 if none
 __device__ __forceinline__ int meta_rank(const BandView& B, int b) {
@@ -199,18 +200,17 @@ __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, co
     __syncthreads();
     nm = meta_word(B, nr);                   // next brick (its rank arrived during the previous brick)
     nr = meta_rank(B, b + 2 * gridDim.x);    // the brick after
-    // own voxels: thread t takes local indices 4t .. 4t+3 (one lookup word, one x-row of the tile)
-    const int l0 = 4 * threadIdx.x;
-    const MetaWord m = sm[0][l0 >> 5];
-    const uint32_t bits = m.bits >> (l0 & 31);
-    int i = m.base + __popc(m.bits & ((1u << (l0 & 31)) - 1u));
-    const int c0 = own_tile(l0);
-    int idx[4];
-    float q[4];
+    // own voxels: thread t takes local indices t + 128 s (consecutive lanes, consecutive tile cells)
+    int idx[4], c[4];
+    float q[4], xv[4], hv[3];
+    int tp[3];
+    // issue every load of the brick before the first shared-memory store uses one
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      idx[s] = ((bits >> s) & 1u) ? i++ : -1;
-      tile[c0 + s] = idx[s] >= 0 ? __ldg(x + idx[s]) : 0.0f;
+      const int l = threadIdx.x + BT * s;
+      idx[s] = slot_index(sm, 0, l);
+      c[s] = own_tile(l);
+      xv[s] = idx[s] >= 0 ? __ldg(x + idx[s]) : 0.0f;
       q[s] = idx[s] >= 0 ? __ldg(qd + idx[s]) : 0.0f;
     }
     // halo: slot h = face f (warp-uniform), face coordinates (u, v)
@@ -218,12 +218,17 @@ __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, co
     for (int s = 0; s < 3; ++s) {
       const int h = threadIdx.x + BT * s, f = h >> 6, u = h & 7, v = (h >> 3) & 7;
       const int j = slot_index(sm, 1 + f, c_halo[f][0] + u * c_halo[f][1] + v * c_halo[f][2]);
-      tile[c_halo[f][3] + u * c_halo[f][4] + v * c_halo[f][5]] = j >= 0 ? __ldg(x + j) : 0.0f;
+      tp[s] = c_halo[f][3] + u * c_halo[f][4] + v * c_halo[f][5];
+      hv[s] = j >= 0 ? __ldg(x + j) : 0.0f;
     }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) tile[c[s]] = xv[s];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) tile[tp[s]] = hv[s];
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 4; ++s)
-      if (idx[s] >= 0) y[idx[s]] = q[s] * tile[c0 + s] - lam * nsum(tile, c0 + s);
+      if (idx[s] >= 0) y[idx[s]] = q[s] * tile[c[s]] - lam * nsum(tile, c[s]);
   }
 }
 
@@ -347,8 +352,8 @@ __global__ void __launch_bounds__(BT) k_cg_init(const SolveArgs<T>* __restrict__
 // One single-reduction PCG iteration (see the file comment); (r, w, s) read
 // from buffer `in`, written to buffer 1 - in; p, x in place.
 template <class T>
-__global__ void __launch_bounds__(BT, 8) k_cg(const SolveArgs<T>* __restrict__ A, int in, PcgState* st,
-                                           cudaGraphConditionalHandle handle) {
+__global__ void __launch_bounds__(BT, CG_OCC) k_cg(const SolveArgs<T>* __restrict__ A, int in, PcgState* st,
+                                                  cudaGraphConditionalHandle handle) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->nexec += 1;
     unsigned g = atomicAdd(&st->guard, 1u);
@@ -376,10 +381,15 @@ __global__ void __launch_bounds__(BT, 8) k_cg(const SolveArgs<T>* __restrict__ A
   const float* __restrict__ qd = A->qd;
   // inner products: per-brick partial sums in T, accumulated in FP64
   double acc[3] = {0.0, 0.0, 0.0};
+  // lookup words of the next brick fetched during the current one (as in k_spmv)
+  MetaWord nm = meta_word(B, meta_rank(B, blockIdx.x));
+  int nr = meta_rank(B, blockIdx.x + gridDim.x);
   for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
     __syncthreads();
-    load_meta(B, b, sm);
+    if (threadIdx.x < 7 * 16) sm[threadIdx.x >> 4][threadIdx.x & 15] = nm;
     __syncthreads();
+    nm = meta_word(B, nr);
+    nr = meta_rank(B, b + 2 * gridDim.x);
     int idx[4];
     T rn[4], un[4];
 #pragma unroll
@@ -564,8 +574,8 @@ static bf_status get_solver(bf_ctx* ctx, bf_band* b, SolveGraph** out) {
     BF_CK(cudaStreamCreateWithFlags(&g->capstream, cudaStreamNonBlocking));
     BF_CK(cudaStreamBeginCaptureToGraph(g->capstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const SolveArgs<T>* A = (const SolveArgs<T>*)g->d_args;
-    k_cg<T><<<NCTA, BT, 0, g->capstream>>>(A, 0, g->st, h);
-    k_cg<T><<<NCTA, BT, 0, g->capstream>>>(A, 1, g->st, h);
+    k_cg<T><<<CG_NCTA, BT, 0, g->capstream>>>(A, 0, g->st, h);
+    k_cg<T><<<CG_NCTA, BT, 0, g->capstream>>>(A, 1, g->st, h);
     cudaGraph_t ob;
     cudaError_t e = cudaStreamEndCapture(g->capstream, &ob);
     if (e != cudaSuccess) return bf_fail(ctx, BF_ECUDA, "capture PCG body", cudaGetErrorString(e));
@@ -584,7 +594,7 @@ static bf_status get_solver(bf_ctx* ctx, bf_band* b, SolveGraph** out) {
     BF_CK(cudaMalloc(&h.p, n * sizeof(T)));
     BF_CK(cudaMalloc(&h.x, n * sizeof(T)));
     BF_CK(cudaMalloc(&h.x64, n * sizeof(double)));
-    BF_CK(cudaMalloc(&h.part, (size_t)3 * NCTA * sizeof(double)));
+    BF_CK(cudaMalloc(&h.part, (size_t)3 * (NCTA > CG_NCTA ? NCTA : CG_NCTA) * sizeof(double)));
     g->cap = n;
   }
   h.B = band_view(b);

@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--rhs-block", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-object", action="store_true",
+                    help="skip the 512^3 object-sequence measurements (SpMV vs HBM peak, batched vs unbatched)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget (s)")
     ap.add_argument("--kernel", default=None,
                     choices=["block_iter", "spmv", "net_forward", "net_train", "net_conv", "net_conv_mma", "net_wgrad"],
@@ -330,6 +332,10 @@ def run_ours(args, world, rank, local):
                "note": "build_band + integrate_depth + solve_mean + estimate_variance from pinned host frames "
                        "to host mu and s (frames staged by each of the two calls that read them)"}
 
+    obj = None
+    if world == 1 and not args.no_object:
+        obj = object_sequence(ctx, stream, args.tol, hbm, peak_kind)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         est, cores, sample, k = oracle_sample(w, oracle_system(w), args.tol, args.K, args.cpu_seconds)
@@ -349,9 +355,81 @@ def run_ours(args, world, rank, local):
                                  "solve_mean": mean_t[2], "estimate_variance": mean_t[3],
                                  "extract_surface": mean_t[4], "score_views": mean_t[5]},
                 "iters": {"mean": info["mean_iters"], "variance_total": info["var_iters"]},
-                "roofline": roof, "spmv": spmv, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roof, "spmv": spmv, "object_sequence": obj, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "wall_s": round(wall, 3)}
         print(json.dumps(line), flush=True)
+
+
+def object_sequence(ctx, stream, tol, hbm, peak_kind):
+    """The 200-frame object sequence (512^3 blob, band +-24, 7.2 M voxels):
+    single-RHS SpMV against the HBM peak (L2 written between launches, median
+    of 20), and time to posterior (mean + 128-probe variance at tol) in three
+    forms: the probes one at a time (unbatched single-RHS PCG), block PCG, and
+    block PCG with the mean warm-started by the learned network (trained here
+    on seeded sphere instances) and the network's variance surrogate judged."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2602_19697_gb300 import bfsdf, learned
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = synth.make_workload("blob512", threads=os.cpu_count() or 0)
+    depth, poses = torch.from_numpy(w.depth).to(dev), torch.from_numpy(w.poses).to(dev)
+    band = ctx.build_band_w(w, depth, poses)
+    band.integrate_depth(depth, poses, w.intr)
+    N, NB = band.N, band.NB
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ms = []
+    for i in range(20):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+        stream.synchronize()
+        ms.append(band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=1))
+    nbytes = N * 12 + NB * 152
+    spmv_gbs = nbytes / (float(np.median(ms)) * 1e-3) / 1e9
+
+    def posterior(rhs_block, net=None):
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            mu, s = torch.empty(N, device=dev), torch.empty(N, device=dev)
+            flush.zero_()
+            e0.record(stream)
+            if net is None:
+                im = band.solve_mean(mu, rel_tol=tol)
+                iv = band.estimate_variance(s, K=128, seed=0, rel_tol=tol, rhs_block=rhs_block)
+                acc = None
+            else:
+                lsh = torch.empty(N, device=dev)
+                net.forward(band, mu, lsh)
+                im = band.solve_mean(mu, rel_tol=tol, warm=True)
+                iv, _, _, acc = band.surrogate_variance(lsh, s, K=128, K_judge=16, seed=0, rel_tol=tol,
+                                                        rhs_block=rhs_block)
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1), im.iters, iv.iters, acc
+
+    plain_ms, plain_mi, plain_vi, _ = posterior(1)
+    posterior(32)
+    block_ms, block_mi, block_vi, _ = posterior(32)
+    data = [learned.make_example(ctx, synth.make_workload("sphere64", variant=i)) for i in range(50)]
+    net = bfsdf.Net(ctx, seed=0)
+    learned.train(net, data, epochs=20, lr=1e-3)
+    posterior(32, net)
+    warm_ms, warm_mi, warm_vi, acc = posterior(32, net)
+    band.free()
+    return {"workload": f"blob512: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, {w.T} views "
+                        f"{w.intr[4]}x{w.intr[5]}, K=128 probes, rel_tol {tol:g}",
+            "N_band": N, "bricks": NB,
+            "spmv": {"kernel": "k_spmv (7-point SpMV, single RHS, brick tiles with shared-memory halo)",
+                     "achieved": round(spmv_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(spmv_gbs / hbm, 4),
+                     "peak_kind": peak_kind, "ms_median": round(float(np.median(ms)), 5), "bytes": nbytes,
+                     "l2": "1 GB written before each of 20 single launches; median"},
+            "posterior_ms": {"unbatched_single_rhs_pcg": round(plain_ms, 3), "block_pcg_r32": round(block_ms, 3),
+                             "block_pcg_learned_warm_start": round(warm_ms, 3)},
+            "iters": {"unbatched": [plain_mi, plain_vi], "block": [block_mi, block_vi],
+                      "learned": [warm_mi, warm_vi]},
+            "surrogate_bricks_accepted": acc}
 
 
 def run_kernel(args):

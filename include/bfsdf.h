@@ -158,7 +158,9 @@ bf_status bf_solve_mean(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter
  * top bit of SplitMix64(SplitMix64(seed) ^ k * 0xD1B54A32D192ED03 ^ lin_j)
  * is 0, else -1 (lin_j the linear voxel index).  The K solves run as block
  * PCG over rhs_block columns at a time (8, 16 or 32; 0 = library choice),
- * every column to rel_tol as in bf_solve_mean.
+ * every column to rel_tol as in bf_solve_mean; rhs_block = 1 solves the
+ * probes one at a time with bf_solve_mean's single right-hand-side solver
+ * (the unbatched form, for comparison).
  *   s [N] float (voxels^2); total_iters (host, may be NULL) = sum over
  *   probes of their iteration counts.
  * Errors as bf_solve_mean; BF_EINVAL for K < 1 or an unsupported block. */

@@ -312,8 +312,8 @@ bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, do
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_estimate_variance: call bf_integrate_depth first");
   if (K < 1 || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: need K >= 1, 0 < rel_tol < 1, 1 <= max_iter <= 1e7");
-  if (rhs_block != 0 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
-    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: rhs_block must be 0, 8, 16 or 32");
+  if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: rhs_block must be 0, 1, 8, 16 or 32");
   float* ds;
   bool host;
   BF_TRY(stage_out(ctx, s, b->N, WS_OUT1, &ds, &host));
@@ -331,8 +331,8 @@ bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* b, int k_begin, int k
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_estimate_variance_range: call bf_integrate_depth first");
   if (k_begin < 0 || k_end <= k_begin || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: need 0 <= k_begin < k_end, 0 < rel_tol < 1");
-  if (rhs_block != 0 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
-    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: rhs_block must be 0, 8, 16 or 32");
+  if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: rhs_block must be 0, 1, 8, 16 or 32");
   float* ds;
   bool host;
   BF_TRY(stage_out(ctx, s_sum, b->N, WS_OUT1, &ds, &host));

@@ -1015,6 +1015,72 @@ bf_status bench_block_iter(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms)
   return bf_fail(ctx, BF_EINVAL, "R must be 8, 16 or 32");
 }
 
+// One probe vector z_k (the same counter-based Rademacher values as k_probes)
+__global__ void k_probe1(int N, const int32_t* __restrict__ lin, uint64_t mseed, int k, float* __restrict__ z) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const uint64_t v = mix64(mseed ^ ((uint64_t)k * 0xD1B54A32D192ED03ULL) ^ (uint64_t)(uint32_t)lin[i]);
+    z[i] = (v >> 63) ? -1.0f : 1.0f;
+  }
+}
+
+// s_acc += z (.) x, sq += (z (.) x)^2 if sq
+__global__ void k_hutch1(int N, const float* __restrict__ z, const float* __restrict__ x, double* __restrict__ sacc,
+                         double* __restrict__ sq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const double t = (double)z[i] * (double)x[i];
+    sacc[i] += t;
+    if (sq) sq[i] += t * t;
+  }
+}
+
+// The probes one at a time as single right-hand-side solves (the unbatched
+// form of the estimator, for comparison with the block solver).
+static bf_status variance_single(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
+                                 int max_iter, float* s_out, int* total_iters, double* sq, double* s1) {
+  cudaStream_t s = ctx->stream;
+  const int N = (int)b->N;
+  float *z = nullptr, *x = nullptr;
+  double* sacc = nullptr;
+  bf_status r = BF_OK;
+  if ((r = dev_alloc_t(ctx, &z, N)) || (r = dev_alloc_t(ctx, &x, N)) || (r = dev_alloc_t(ctx, &sacc, N))) {
+    dev_free(s, z);
+    dev_free(s, x);
+    return r;
+  }
+  uint64_t mseed = 0;
+  {  // host copy of the probe seed mix (same function as the device)
+    uint64_t zz = seed + 0x9E3779B97F4A7C15ULL;
+    zz = (zz ^ (zz >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    zz = (zz ^ (zz >> 27)) * 0x94D049BB133111EBULL;
+    mseed = zz ^ (zz >> 31);
+  }
+  int tot = 0;
+  if (cudaMemsetAsync(sacc, 0, (size_t)N * 8, s) != cudaSuccess) r = bf_fail(ctx, BF_ECUDA, "memset");
+  for (int k = kb; k < ke && r == BF_OK; ++k) {
+    k_probe1<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, b->lin, mseed, k, z);
+    count_launch();
+    int it = 0;
+    r = solve_rhs_impl(ctx, b, z, tol, max_iter, x, &it, nullptr);
+    tot += it;
+    if (r == BF_OK) {
+      k_hutch1<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, z, x, sacc, sq);
+      count_launch();
+    }
+  }
+  if (r == BF_OK) {
+    k_finish<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, sacc, scale, s_out);
+    count_launch();
+    if (s1 && cudaMemcpyAsync(s1, sacc, (size_t)N * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      r = bf_fail(ctx, BF_ECUDA, "copy probe sums");
+    if (cudaStreamSynchronize(s) != cudaSuccess) r = bf_fail(ctx, BF_ECUDA, "variance_single");
+  }
+  dev_free(s, z);
+  dev_free(s, x);
+  dev_free(s, sacc);
+  if (total_iters) *total_iters = tot;
+  return r;
+}
+
 // probes k in [kb, ke); s = scale * sum_k z_k (.) Q^-1 z_k; sq (device, may be
 // null) += sum_k (z_k (.) Q^-1 z_k)^2; s1 (device, may be null) = the FP64 sum
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
@@ -1026,10 +1092,11 @@ bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, u
   }
   const int K = ke - kb;
   if (R == 0) R = K >= 32 ? 32 : (K >= 16 ? 16 : 8);
+  if (R == 1) return variance_single(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
   switch (R) {
     case 8: return variance_t<8>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
     case 16: return variance_t<16>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
     case 32: return variance_t<32>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
   }
-  return bf_fail(ctx, BF_EINVAL, "rhs_block must be 0, 8, 16 or 32");
+  return bf_fail(ctx, BF_EINVAL, "rhs_block must be 0, 1, 8, 16 or 32");
 }

@@ -165,6 +165,8 @@ bf_status band_assemble(bf_ctx* ctx, bf_band* b);
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
 bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,
                           double* relres);
+bf_status solve_rhs_impl(bf_ctx* ctx, bf_band* b, const float* rhs, double tol, int max_iter, float* x, int* iters,
+                         double* relres);
 bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
                         int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq = nullptr,
                         double* s1 = nullptr);

@@ -1059,8 +1059,8 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_surrogate_variance: call bf_integrate_depth first");
   if (K_judge < 2 || K <= K_judge || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
     return bf_fail(ctx, BF_EINVAL, "bf_surrogate_variance: need 2 <= K_judge < K, 0 < rel_tol < 1");
-  if (rhs_block != 0 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
-    return bf_fail(ctx, BF_EINVAL, "bf_surrogate_variance: rhs_block must be 0, 8, 16 or 32");
+  if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
+    return bf_fail(ctx, BF_EINVAL, "bf_surrogate_variance: rhs_block must be 0, 1, 8, 16 or 32");
   if (n_accepted) *n_accepted = 0;
   if (total_iters) *total_iters = 0;
   if (b->N == 0) return BF_OK;

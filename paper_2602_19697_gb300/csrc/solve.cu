@@ -547,7 +547,7 @@ void solve_graph_free(SolveGraph* g) {
 }
 
 template <class T>
-static bf_status get_solver(bf_ctx* ctx, bf_band* b, SolveGraph** out) {
+static bf_status get_solver(bf_ctx* ctx, bf_band* b, SolveGraph** out, const float* rhs = nullptr) {
   const bool fp64 = sizeof(T) == 8;
   SolveGraph*& g = ctx->sgl[fp64 ? 1 : 0];
   cudaStream_t s = ctx->stream;
@@ -600,7 +600,7 @@ static bf_status get_solver(bf_ctx* ctx, bf_band* b, SolveGraph** out) {
   h.B = band_view(b);
   h.lam = (float)b->prm.lambda;
   h.qd = b->qd;
-  h.rhs = b->rhs;
+  h.rhs = rhs ? rhs : b->rhs;  // the band's h, or another right-hand side
   // the previous upload from h_pin has completed: every solve ends with a sync
   memcpy(g->h_pin, &h, sizeof(h));
   BF_CK(cudaMemcpyAsync(g->d_args, g->h_pin, sizeof(h), cudaMemcpyHostToDevice, s));
@@ -610,10 +610,10 @@ static bf_status get_solver(bf_ctx* ctx, bf_band* b, SolveGraph** out) {
 
 template <class T>
 static bf_status solve_t(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,
-                         double* relres) {
+                         double* relres, const float* rhs = nullptr) {
   cudaStream_t s = ctx->stream;
   SolveGraph* g = nullptr;
-  BF_TRY(get_solver<T>(ctx, b, &g));
+  BF_TRY(get_solver<T>(ctx, b, &g, rhs));
   SolveArgs<T>& h = host_args<T>(g);
   const SolveArgs<T>* A = (const SolveArgs<T>*)g->d_args;
   const int N = (int)b->N;
@@ -669,6 +669,17 @@ bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, uns
   }
   if (flags & BF_SOLVE_FP64) return solve_t<double>(ctx, b, tol, max_iter, flags, mu, iters, relres);
   return solve_t<float>(ctx, b, tol, max_iter, flags, mu, iters, relres);
+}
+
+// Q x = rhs for another right-hand side (FP32 vectors, FP64 refinement), x0 = 0
+bf_status solve_rhs_impl(bf_ctx* ctx, bf_band* b, const float* rhs, double tol, int max_iter, float* x, int* iters,
+                         double* relres) {
+  if (b->N == 0) {
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return BF_OK;
+  }
+  return solve_t<float>(ctx, b, tol, max_iter, 0u, x, iters, relres, rhs);
 }
 
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {

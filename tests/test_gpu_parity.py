@@ -163,7 +163,8 @@ def test_solver_edge_cases():
 
 
 @pytest.mark.parametrize("name,K,R", [("sphere32_small", 16, 8), ("sphere32_small", 20, 16),
-                                      ("sphere64", 16, 16), ("union128", 8, 32), ("blob128_b5", 8, 8)])
+                                      ("sphere64", 16, 16), ("union128", 8, 32), ("blob128_b5", 8, 8),
+                                      ("sphere32_small", 6, 1)])
 def test_variance_matches_oracle_for_identical_probes(name, K, R):
     c = case(name)
     w = c["w"]
@@ -183,7 +184,7 @@ def test_variance_does_not_depend_on_the_block_width():
     gb, depth, poses = gpu_band(w)
     gb.integrate_depth(depth, poses, w.intr)
     out = []
-    for R in (8, 16, 32):
+    for R in (8, 16, 32, 1):
         s = torch.empty(gb.N, device="cuda")
         gb.estimate_variance(s, K=32, seed=9, rel_tol=1e-8, rhs_block=R)
         out.append(s.cpu().numpy())

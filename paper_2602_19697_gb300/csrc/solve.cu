@@ -156,22 +156,12 @@ __device__ __forceinline__ T nsum(const T* t, int c) {
   return ((t[c - 1] + t[c + 1]) + (t[c - 10] + t[c + 10])) + (t[c - 100] + t[c + 100]);
 }
 
-// Halo slots of a face f = 2 axis + side (side 0: the -axis neighbour's
-// layer 7, side 1: the +axis neighbour's layer 0), at face coordinates (u, v)
-// along the two other axes in increasing order: local index in the neighbour
-// brick = [0] + u [1] + v [2], position in the 10^3 tile = [3] + u [4] + v [5]
-// (the same mapping as halo_slot).
-__constant__ int c_halo[6][6] = {
-    {7, 8, 64, 10 + 100, 10, 100},       {0, 8, 64, 9 + 10 + 100, 10, 100},
-    {56, 1, 64, 1 + 100, 1, 100},        {0, 1, 64, 1 + 90 + 100, 1, 100},
-    {448, 1, 8, 1 + 10, 1, 10},          {0, 1, 8, 1 + 10 + 900, 1, 10},
-};
-
-// y = Q x (plain SpMV, FP32).  A CTA walks bricks b, b + grid, ...; the
-// lookup words of the next brick and its six neighbours are fetched into
-// registers while the current brick's x is gathered, and the neighbour ranks
-// one brick further ahead, so a brick costs one round trip to memory.
-constexpr int SPMV_OCC = 12;  // resident CTAs per SM (40 registers x 128 threads)
+// y = Q x (plain SpMV, FP32).  A CTA walks bricks b, b + grid, ...; the x
+// and Q_jj loads of the next brick are issued while the current brick is
+// formed, its lookup words (own and six neighbours) one brick earlier and the
+// neighbour ranks one brick earlier still, so no round trip to memory is
+// waited for in the steady state.
+constexpr int SPMV_OCC = 8;  // resident CTAs per SM (64 registers x 128 threads)
 constexpr int CG_OCC = 8, CG_NCTA = 152 * CG_OCC;  // k_cg: resident CTAs per SM, grid
 
 // rank of brick b (thread's slot 0) or of its face neighbour (slots 1-6); -1 if none
@@ -188,47 +178,127 @@ __device__ __forceinline__ MetaWord meta_word(const BandView& B, int r) {
   return m;
 }
 
+// The SpMV tile: pitch 24 in x (own lx at x = lx + 4, so a thread's four
+// voxels are one aligned float4 and eight lanes' float4 fall in distinct
+// banks), 10 rows in y and z (own ly, lz at ly + 1, lz + 1).  Halo face f at
+// face coordinates (u, v): local index in the neighbour brick [0] + u [1] +
+// v [2], tile position [3] + u [4] + v [5] (faces -x, +x, -y, +y, -z, +z;
+// (u, v) are the two other axes in increasing order).
+constexpr int SP_PY = 24, SP_PZ = 240, SP_TILE = 2400;
+__constant__ int c_halo24[6][6] = {
+    {7, 8, 64, 267, 24, 240},   {0, 8, 64, 276, 24, 240},   {56, 1, 64, 244, 1, 240},
+    {0, 1, 64, 460, 1, 240},    {448, 1, 8, 28, 1, 24},     {0, 1, 8, 2188, 1, 24},
+};
+
+// Loads of one brick, issued one brick ahead of their use.  Thread t owns
+// local indices 4t .. 4t+3 (one lookup word, one x-row).
+struct SpmvLoads {
+  int i0;       // compact index of the first present voxel of the four
+  uint32_t m4;  // presence bits of the four voxels
+  float4 xv, q;
+  float hv[3];
+  int tp[3];
+};
+
+__device__ __forceinline__ void spmv_issue(const MetaWord (*sm)[16], const float* __restrict__ x,
+                                           const float* __restrict__ qd, SpmvLoads& L) {
+  const int l0 = 4 * threadIdx.x;
+  const MetaWord m = sm[0][l0 >> 5];
+  L.m4 = (m.bits >> (l0 & 31)) & 0xFu;
+  L.i0 = m.base + __popc(m.bits & ((1u << (l0 & 31)) - 1u));
+  float xs[4], qs[4];
+  int i = L.i0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const bool on = (L.m4 >> s) & 1u;
+    xs[s] = on ? __ldg(x + i) : 0.0f;
+    qs[s] = on ? __ldg(qd + i) : 0.0f;
+    i += on;
+  }
+  L.xv = make_float4(xs[0], xs[1], xs[2], xs[3]);
+  L.q = make_float4(qs[0], qs[1], qs[2], qs[3]);
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {  // halo: slot h = face f (warp-uniform), face coordinates (u, v)
+    const int h = threadIdx.x + BT * s, f = h >> 6, u = h & 7, v = (h >> 3) & 7;
+    const int j = slot_index(sm, 1 + f, c_halo24[f][0] + u * c_halo24[f][1] + v * c_halo24[f][2]);
+    L.tp[s] = c_halo24[f][3] + u * c_halo24[f][4] + v * c_halo24[f][5];
+    L.hv[s] = j >= 0 ? __ldg(x + j) : 0.0f;
+  }
+}
+
+// bring bytes of v[i0 .. i1) into L2 as whole lines (bulk prefetch of the 16-byte granules inside the range)
+__device__ __forceinline__ void prefetch_range(const float* v, int64_t i0, int64_t i1) {
+  const uint64_t a0 = ((uint64_t)(v + i0) + 15u) & ~(uint64_t)15u, a1 = (uint64_t)(v + i1) & ~(uint64_t)15u;
+  if (a1 > a0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
+}
+
+// Software pipeline over the CTA's bricks b0, b1 = b0 + grid, ...: in the
+// iteration of brick b_i the tile receives b_i's values (loaded during the
+// previous iteration), the loads of b_{i+1} are issued (its lookup words
+// fetched one iteration earlier still), and y of b_i is formed, four voxels
+// per thread from float4 reads of the tile; the neighbour sum keeps the
+// order ((x-1 + x+1) + (y-1 + y+1)) + (z-1 + z+1).
 __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, const float* __restrict__ qd,
                                                        const float* __restrict__ x, float* __restrict__ y) {
-  __shared__ float tile[1000];
-  __shared__ MetaWord sm[7][16];
-  MetaWord nm = meta_word(B, meta_rank(B, blockIdx.x));
-  int nr = meta_rank(B, blockIdx.x + gridDim.x);
-  for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
-    __syncthreads();  // the previous brick's readers of tile and sm are done
-    if (threadIdx.x < 7 * 16) sm[threadIdx.x >> 4][threadIdx.x & 15] = nm;
-    __syncthreads();
-    nm = meta_word(B, nr);                   // next brick (its rank arrived during the previous brick)
-    nr = meta_rank(B, b + 2 * gridDim.x);    // the brick after
-    // own voxels: thread t takes local indices t + 128 s (consecutive lanes, consecutive tile cells)
-    int idx[4], c[4];
-    float q[4], xv[4], hv[3];
-    int tp[3];
-    // issue every load of the brick before the first shared-memory store uses one
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int l = threadIdx.x + BT * s;
-      idx[s] = slot_index(sm, 0, l);
-      c[s] = own_tile(l);
-      xv[s] = idx[s] >= 0 ? __ldg(x + idx[s]) : 0.0f;
-      q[s] = idx[s] >= 0 ? __ldg(qd + idx[s]) : 0.0f;
+  __shared__ __align__(16) float tile[SP_TILE];
+  __shared__ MetaWord sm[2][7][16];
+  const int g = gridDim.x;
+  if (threadIdx.x < 7 * 16) sm[0][threadIdx.x >> 4][threadIdx.x & 15] = meta_word(B, meta_rank(B, blockIdx.x));
+  MetaWord nm = meta_word(B, meta_rank(B, blockIdx.x + g));  // lookup words of b_1
+  int nr = meta_rank(B, blockIdx.x + 2 * g);                   // ranks for b_2
+  __syncthreads();
+  SpmvLoads cur, nxt;
+  if ((int)blockIdx.x < B.NB) spmv_issue(sm[0], x, qd, cur);
+  // x and Q_jj of the brick two ahead are prefetched into L2 as whole lines (its range one iteration earlier)
+  int2 pr = make_int2(0, 0);
+  if (threadIdx.x == 0 && (int)blockIdx.x + 2 * g < B.NB)
+    pr = make_int2(__ldg(B.off + blockIdx.x + 2 * g), __ldg(B.off + blockIdx.x + 2 * g + 1));
+  const int l0 = 4 * threadIdx.x;
+  const int t0 = ((l0 & 7) + 4) + SP_PY * (((l0 >> 3) & 7) + 1) + SP_PZ * ((l0 >> 6) + 1);
+  int it = 0;
+  for (int b = blockIdx.x; b < B.NB; b += g, ++it) {
+    if (threadIdx.x == 0) {
+      if (pr.y > pr.x) {
+        prefetch_range(x, pr.x, pr.y);
+        prefetch_range(qd, pr.x, pr.y);
+      }
+      const int bn = b + 3 * g;
+      pr = bn < B.NB ? make_int2(__ldg(B.off + bn), __ldg(B.off + bn + 1)) : make_int2(0, 0);
     }
-    // halo: slot h = face f (warp-uniform), face coordinates (u, v)
+    const int pn = (it + 1) & 1;
+    // tile <- b's values; lookup words of the next brick into the other buffer
+    *reinterpret_cast<float4*>(tile + t0) = cur.xv;
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-      const int h = threadIdx.x + BT * s, f = h >> 6, u = h & 7, v = (h >> 3) & 7;
-      const int j = slot_index(sm, 1 + f, c_halo[f][0] + u * c_halo[f][1] + v * c_halo[f][2]);
-      tp[s] = c_halo[f][3] + u * c_halo[f][4] + v * c_halo[f][5];
-      hv[s] = j >= 0 ? __ldg(x + j) : 0.0f;
-    }
-#pragma unroll
-    for (int s = 0; s < 4; ++s) tile[c[s]] = xv[s];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) tile[tp[s]] = hv[s];
+    for (int s = 0; s < 3; ++s) tile[cur.tp[s]] = cur.hv[s];
+    if (threadIdx.x < 7 * 16) sm[pn][threadIdx.x >> 4][threadIdx.x & 15] = nm;
     __syncthreads();
+    if (b + g < B.NB) spmv_issue(sm[pn], x, qd, nxt);
+    nm = meta_word(B, nr);
+    nr = meta_rank(B, b + 3 * g);
+    if (cur.m4) {
+      const float4 c = *reinterpret_cast<const float4*>(tile + t0);
+      const float xl = tile[t0 - 1], xr = tile[t0 + 4];
+      const float4 ym = *reinterpret_cast<const float4*>(tile + t0 - SP_PY);
+      const float4 yp = *reinterpret_cast<const float4*>(tile + t0 + SP_PY);
+      const float4 zm = *reinterpret_cast<const float4*>(tile + t0 - SP_PZ);
+      const float4 zp = *reinterpret_cast<const float4*>(tile + t0 + SP_PZ);
+      const float xm[4] = {xl, c.x, c.y, c.z}, xp[4] = {c.y, c.z, c.w, xr};
+      const float cc[4] = {c.x, c.y, c.z, c.w}, qq[4] = {cur.q.x, cur.q.y, cur.q.z, cur.q.w};
+      const float ym4[4] = {ym.x, ym.y, ym.z, ym.w}, yp4[4] = {yp.x, yp.y, yp.z, yp.w};
+      const float zm4[4] = {zm.x, zm.y, zm.z, zm.w}, zp4[4] = {zp.x, zp.y, zp.z, zp.w};
+      int i = cur.i0;
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (idx[s] >= 0) y[idx[s]] = q[s] * tile[c[s]] - lam * nsum(tile, c[s]);
+      for (int s = 0; s < 4; ++s) {
+        if ((cur.m4 >> s) & 1u) {
+          const float ns = ((xm[s] + xp[s]) + (ym4[s] + yp4[s])) + (zm4[s] + zp4[s]);
+          y[i] = qq[s] * cc[s] - lam * ns;
+          ++i;
+        }
+      }
+    }
+    __syncthreads();  // tile and this iteration's lookup buffer are free again
+    cur = nxt;
   }
 }
 

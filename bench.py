@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--workload", default="union256")
     ap.add_argument("--K", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--rhs-block", type=int, default=32)
+    ap.add_argument("--rhs-block", type=int, default=0, help="probe block width (0 = the library's autotuner)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-object", action="store_true",
@@ -283,20 +283,21 @@ def run_ours(args, world, rank, local):
     hbm, peak_kind = peaks()
     band = ctx.build_band_w(w, depth, poses)
     band.integrate_depth(depth, poses, w.intr)
+    R_used, tune_ms = (R, None) if R else band.autotune_rhs_block(args.K)  # the width the timed steps used
     s = torch.empty(band.N, device=dev)
-    band.estimate_variance(s, K=R, seed=0, rel_tol=args.tol, rhs_block=R)
-    ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R, reps=50)
+    band.estimate_variance(s, K=R_used, seed=0, rel_tol=args.tol, rhs_block=R_used)
+    ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R_used, reps=50)
     N, NB = band.N, band.NB
     # algorithmic bytes of one probe-solver iteration (per voxel row of R
     # columns): r, w, s, p, x read and p, x, r', s', w' written (40 B per
     # column), Q_jj and 1/Q_jj read (8 B); the neighbour gathers of the SpMM
     # are not counted (they come from shared memory and L2 by design)
-    bytes_it = N * (R * 40 + 8)
+    bytes_it = N * (R_used * 40 + 8)
     ms_spmv = band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=200)
     bytes_spmv = N * 12 + NB * (128 + 24)   # x, qd read, y written; brick metadata
     achieved = bytes_it / (ms_iter * 1e-3) / 1e9
     roof = {"kernel": "k_blk_it<%d> (one probe-solver iteration: vector updates and w = Q u in one pass, "
-                      "the dominant kernel)" % R, "bound": "hbm",
+                      "the dominant kernel)" % R_used, "bound": "hbm",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "peak_kind": peak_kind, "traffic": None, "bytes_per_launch": bytes_it,
             "ms_per_launch": round(ms_iter, 5)}
@@ -348,7 +349,9 @@ def run_ours(args, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": f"{w.name}: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, "
                                        f"{w.T} views {w.intr[4]}x{w.intr[5]}, K={args.K} probes, rel_tol {args.tol:g}",
-                           "N_band": info["N"], "bricks": info["NB"], "rhs_block": R,
+                           "N_band": info["N"], "bricks": info["NB"], "rhs_block": R_used,
+                           "rhs_block_choice": "autotuned" if not R else "fixed",
+                           "autotune_ms_per_iter_r8_r16_r32": None if tune_ms is None else [round(float(v), 5) for v in tune_ms],
                            "l2": "512 MB buffer written between timed steps",
                            "parallelism": f"replicas x{world}"},
                 "breakdown_ms": {"build_band": mean_t[0], "integrate_depth": mean_t[1],
@@ -449,7 +452,7 @@ def run_kernel(args):
     depth, poses = torch.from_numpy(w.depth).cuda(), torch.from_numpy(w.poses).cuda()
     band = ctx.build_band_w(w, depth, poses)
     band.integrate_depth(depth, poses, w.intr)
-    N, NB, R = band.N, band.NB, args.rhs_block
+    N, NB, R = band.N, band.NB, (args.rhs_block or 32)
     out = {"kernel": args.kernel, "workload": args.workload, "N_band": N, "bricks": NB}
     if args.kernel in ("block_iter", "spmv"):
         which = bfsdf.BF_KERNEL_BLOCK_ITER if args.kernel == "block_iter" else bfsdf.BF_KERNEL_SPMV

@@ -157,7 +157,8 @@ bf_status bf_solve_mean(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter
  * s = (1/K) sum_k z_k (.) Q^-1 z_k with Rademacher probes z_k(j) = +1 if the
  * top bit of SplitMix64(SplitMix64(seed) ^ k * 0xD1B54A32D192ED03 ^ lin_j)
  * is 0, else -1 (lin_j the linear voxel index).  The K solves run as block
- * PCG over rhs_block columns at a time (8, 16 or 32; 0 = library choice),
+ * PCG over rhs_block columns at a time (8, 16 or 32; 0 = library choice by
+ * bf_autotune_rhs_block),
  * every column to rel_tol as in bf_solve_mean; rhs_block = 1 solves the
  * probes one at a time with bf_solve_mean's single right-hand-side solver
  * (the unbatched form, for comparison).
@@ -201,6 +202,19 @@ bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris);
  * (host or device); *best (host, may be NULL) = argmax, lowest index on ties. */
 bf_status bf_score_views(bf_ctx* ctx, const bf_band* band, const float* mu, const float* s,
                          const float* cand_poses, int V, const bf_intrinsics* K, double eps, double* U, int* best);
+
+/* Autotuner of the probe block width (the library choice rhs_block = 0 of
+ * bf_estimate_variance uses it): times one block-PCG iteration on this band
+ * at R = 8, 16, 32 (R not wider than K needs) and returns the R that
+ * minimises ceil(K / R) x (time of one iteration at R).  The paper has no
+ * counterpart (it solves probes one by one).  Choices are cached in the
+ * context per (floor(log2 N), K class) unless force != 0, and, when the
+ * environment variable BFSDF_TUNE_CACHE names a file, persisted there as
+ * JSON lines and read back by later contexts on the same GPU model.
+ *   *rhs_block (host) receives the choice; ms_per_iter (host [3], may be
+ *   NULL) the measured ms per iteration at R = 8, 16, 32 (0 = not tried).
+ * Overwrites the probe solver's workspace (no solve is in progress). */
+bf_status bf_autotune_rhs_block(bf_ctx* ctx, bf_band* band, int K, int force, int* rhs_block, double* ms_per_iter);
 
 /* Allocation-free mean solve, for callers that must not allocate device
  * memory while they run (a real-time loop with a fixed memory budget, or a

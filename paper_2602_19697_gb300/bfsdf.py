@@ -34,7 +34,7 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_score_views", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
             "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
             "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance",
-            "bf_net_bench"]
+            "bf_net_bench", "bf_autotune_rhs_block"]
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
 BF_NET_BENCH_FORWARD, BF_NET_BENCH_TRAIN, BF_NET_BENCH_CONV, BF_NET_BENCH_WGRAD, BF_NET_BENCH_CONV_MMA = range(5)
@@ -111,6 +111,7 @@ def load_library(path: str = LIB_PATH):
         "bf_surrogate_variance": (i, [vp, vp, vp, i, i, ctypes.c_uint64, d, i, i, u, vp, vp, vp,
                                       ctypes.POINTER(i), ctypes.POINTER(i)]),
         "bf_net_bench": (i, [vp, vp, vp, i, i, ctypes.POINTER(d)]),
+        "bf_autotune_rhs_block": (i, [vp, vp, i, i, ctypes.POINTER(i), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -301,6 +302,14 @@ class Band:
                                                 _ptr(acc), _ptr(stat), ctypes.byref(na), ctypes.byref(it))
         self.ctx.check(st, "bf_surrogate_variance")
         return SolveInfo(it.value, 0.0, st), acc, stat, na.value
+
+    def autotune_rhs_block(self, K: int, force: bool = False):
+        """Probe block width chosen by the library's autotuner; returns (R, ms per iteration at 8, 16, 32)."""
+        R = ctypes.c_int()
+        ms = np.zeros(3, np.float64)
+        self.ctx.check(self.ctx.lib.bf_autotune_rhs_block(self.ctx._p, self._p, int(K), int(bool(force)),
+                                                          ctypes.byref(R), _ptr(ms)), "bf_autotune_rhs_block")
+        return R.value, ms
 
     def extract_surface(self, mu, device="numpy"):
         nv, nt = ctypes.c_int64(), ctypes.c_int64()

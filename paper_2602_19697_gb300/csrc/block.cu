@@ -1091,7 +1091,7 @@ bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, u
     return BF_OK;
   }
   const int K = ke - kb;
-  if (R == 0) R = K >= 32 ? 32 : (K >= 16 ? 16 : 8);
+  if (R == 0) BF_TRY(autotune_rhs_block(ctx, b, K, false, &R, nullptr));  // library choice: measured
   if (R == 1) return variance_single(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
   switch (R) {
     case 8: return variance_t<8>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "bfsdf.h"
 
@@ -33,6 +34,12 @@ enum { WS_STAGE0 = 0, WS_STAGE1, WS_STAGE2, WS_STAGE3, WS_OUT0, WS_OUT1, WS_TMP0
 struct SolveGraph;  // solve.cu
 struct BlockGraph;  // block.cu
 
+// a tuned probe-block width: band size class, probe-count class, choice, ms per iteration at R = 8, 16, 32
+struct TuneEntry {
+  int n_log2, k_class, R;
+  double ms[3];
+};
+
 struct bf_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -48,6 +55,8 @@ struct bf_ctx {
   int8_t* mc_ntri = nullptr;    // device [256]
   BlockGraph* blk[3] = {nullptr, nullptr, nullptr};  // probe solvers, R = 8, 16, 32
   SolveGraph* sgl[2] = {nullptr, nullptr};           // mean solvers, FP32 and FP64
+  std::vector<TuneEntry> tune;                       // autotuned probe-block widths
+  bool tune_loaded = false;
 };
 
 // Per-brick lookup entry: band bits of 32 local voxels and the compact index
@@ -171,6 +180,7 @@ bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, u
                         int max_iter, int R, unsigned flags, float* s, int* total_iters, double* sq = nullptr,
                         double* s1 = nullptr);
 bf_status bench_block_iter(bf_ctx* ctx, bf_band* b, int R, int reps, double* ms);
+bf_status autotune_rhs_block(bf_ctx* ctx, bf_band* b, int K, bool force, int* R_out, double ms_out[3]);
 void solve_graph_free(SolveGraph* g);
 void block_graph_free(BlockGraph* g);
 bf_status mc_impl(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt);

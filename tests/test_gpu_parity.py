@@ -238,3 +238,35 @@ def test_probe_ranges_sum_to_the_full_estimate():
     np.testing.assert_allclose((parts / K).cpu().numpy(), s.cpu().numpy(), rtol=2e-5, atol=0)
     one = estimate_variance_sharded(fn, K, 0, 1)   # one rank: no collective
     np.testing.assert_allclose(one.cpu().numpy(), s.cpu().numpy(), rtol=2e-5, atol=0)
+
+
+def test_autotuner_choice_cache_and_library_default(tmp_path, monkeypatch):
+    c = case("sphere32_small")
+    w = c["w"]
+    path = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("BFSDF_TUNE_CACHE", str(path))
+    from paper_2602_19697_gb300 import bfsdf
+    ctx1 = bfsdf.Context(0)
+    depth, poses = dev(w.depth), dev(w.poses)
+    b1 = ctx1.build_band_w(w, depth, poses)
+    b1.integrate_depth(depth, poses, w.intr)
+    R, ms = b1.autotune_rhs_block(64, force=True)
+    assert R in (8, 16, 32) and np.all(ms > 0)
+    lines = path.read_text().strip().splitlines()
+    assert len(lines) == 1 and f'"R": {R}' in lines[0]
+    # a second context on the same GPU takes the choice from the file without measuring
+    ctx2 = bfsdf.Context(0)
+    b2 = ctx2.build_band_w(w, depth, poses)
+    b2.integrate_depth(depth, poses, w.intr)
+    R2, ms2 = b2.autotune_rhs_block(64)
+    assert R2 == R
+    np.testing.assert_allclose(ms2, ms, rtol=1e-5)
+    assert len(path.read_text().strip().splitlines()) == 1
+    # the library's default block width gives the estimate of that width
+    s0, sR = torch.empty(b2.N, device="cuda"), torch.empty(b2.N, device="cuda")
+    b2.estimate_variance(s0, K=64, seed=2, rel_tol=1e-8, rhs_block=0)
+    b2.estimate_variance(sR, K=64, seed=2, rel_tol=1e-8, rhs_block=R)
+    np.testing.assert_allclose(s0.cpu().numpy(), sR.cpu().numpy(), rtol=1e-6)
+    # a small K never tunes a block wider than it needs
+    Rs, mss = b2.autotune_rhs_block(8, force=True)
+    assert Rs == 8 and mss[1] == 0 and mss[2] == 0

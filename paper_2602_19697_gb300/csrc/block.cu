@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       cudaGraphSetConditional(handle, 0);
     }
   }
-  if (!INIT && !bench && st->all_done) return;
+  if (!bench && st->all_done) return;  // also a start pass after the true residual met the tolerance
   constexpr int Q4 = R / 4;                          // float4 per row
   constexpr int OWN = SP_TR * Q4 / CT;               // own-row float4 per thread
   constexpr int XN = (SP_EMAX * Q4 + CT - 1) / CT;  // external float4 per thread (at most)

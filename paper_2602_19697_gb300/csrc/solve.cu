@@ -364,6 +364,7 @@ __global__ void __launch_bounds__(BT) k_outer(const SolveArgs<T>* __restrict__ A
 // delta = w.u; alpha = gamma/delta.
 template <class T>
 __global__ void __launch_bounds__(BT) k_cg_init(const SolveArgs<T>* __restrict__ A, PcgState* st) {
+  if (st->done) return;  // the true residual already met the tolerance: no correction solve follows
   __shared__ T tile[1000];
   __shared__ MetaWord sm[7][16];
   const BandView& B = A->B;

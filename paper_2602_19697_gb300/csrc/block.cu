@@ -86,6 +86,8 @@ struct BlkArgs {
   const __nv_bfloat16* Z;
   double* part;        // [3][R][NCTA]
   double* part1;       // [2][R][NCTA] pass-1 partials
+  double* hsum;        // [N] sum over the block's columns of z (.) xm, from the last residual pass
+  double* hsq;         // [N] the same for (z (.) xm)^2, or null
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -203,21 +205,46 @@ __global__ void __launch_bounds__(CT) k_blk_outer(const BlkArgs* __restrict__ A,
   int row0, row1;
   cta_rows(N, &row0, &row1);
   float fr = 0.0f, fz = 0.0f;
-  for (int row = row0 + wrp * RPW + lane / R; row < row1; row += nw * RPW) {
-    const size_t o = (size_t)row * R + c;
-    int nb[6];
-    load_nb6(A->nb6, row, nb);
-    float2 ns = make_float2(0.f, 0.f);
+  // warp-uniform trip count: the per-row sums over the columns below are shuffle trees
+  for (int base = row0 + wrp * RPW; base < row1; base += nw * RPW) {
+    const int row = base + lane / R;
+    const bool ok = row < row1;
+    float2 t = make_float2(0.f, 0.f);
+    if (ok) {
+      const size_t o = (size_t)row * R + c;
+      int nb[6];
+      load_nb6(A->nb6, row, nb);
+      float2 ns = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-      if (nb[k] >= 0) ns = ff_add(ns, xm[(size_t)nb[k] * R + c]);
-    const float z = __bfloat162float(A->Z[o]);
-    const float2 qx = ff_add(ff_mul_f(xm[o], __ldg(A->qd + row)), ff_neg(ff_mul_f(ns, lam)));
-    const float2 rf = ff_add_f(ff_neg(qx), z);
-    const float r = __fadd_rn(rf.x, rf.y);
-    A->r[st->par][o] = r;
-    fr += r * r;
-    fz += z * z;
+      for (int k = 0; k < 6; ++k)
+        if (nb[k] >= 0) ns = ff_add(ns, xm[(size_t)nb[k] * R + c]);
+      const float z = __bfloat162float(A->Z[o]);
+      const float2 xo = xm[o];
+      const float2 qx = ff_add(ff_mul_f(xo, __ldg(A->qd + row)), ff_neg(ff_mul_f(ns, lam)));
+      const float2 rf = ff_add_f(ff_neg(qx), z);
+      const float r = __fadd_rn(rf.x, rf.y);
+      A->r[st->par][o] = r;
+      fr += r * r;
+      fz += z * z;
+      t = make_float2(z * xo.x, z * xo.y);  // z = +-1 or 0: exact
+    }
+    // probe sums of this row (kept by the last residual pass of the block): float-float tree over the
+    // columns in a fixed order, then FP64
+    float2 qq = make_float2(0.f, 0.f);
+    if (A->hsq) {
+      const float p0 = __fmul_rn(t.x, t.x);
+      qq = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
+    }
+#pragma unroll
+    for (int o = R / 2; o > 0; o >>= 1) {
+      t = ff_add(t, make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o)));
+      if (A->hsq)
+        qq = ff_add(qq, make_float2(__shfl_xor_sync(0xffffffffu, qq.x, o), __shfl_xor_sync(0xffffffffu, qq.y, o)));
+    }
+    if (ok && c == 0) {
+      A->hsum[row] = (double)t.x + (double)t.y;
+      if (A->hsq) A->hsq[row] = (double)qq.x + (double)qq.y;
+    }
   }
   double acc[2] = {(double)fr, (double)fz};
   column_partials<R, 2>(acc, A->part);
@@ -543,11 +570,12 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   }
 }
 
-// Z[i][c] = Rademacher(seed, k0 + c, lin_i) for c < ncols, 0 beyond; xm = 0
-// and the first correction right-hand side r = z - Q 0 = z
+// Z[i][c] = Rademacher(seed, k0 + c, lin_i) for c < ncols, 0 beyond, and the
+// first correction right-hand side r = z - Q 0 = z (xm = 0 is implied: the
+// first correction is copied into xm rather than added)
 template <int R>
 __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed, int k0, int ncols,
-                         __nv_bfloat16* __restrict__ Z, float2* __restrict__ x, float* __restrict__ r0) {
+                         __nv_bfloat16* __restrict__ Z, float* __restrict__ r0) {
   const int64_t n = (int64_t)N * R;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e / R;
@@ -558,49 +586,7 @@ __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed,
       z = (v >> 63) ? -1.0f : 1.0f;
     }
     Z[e] = __float2bfloat16(z);
-    x[e] = make_float2(0.f, 0.f);
     r0[e] = z;
-  }
-}
-
-// s_acc[i] += sum_c z[i][c] xm[i][c] (float-float sum over the columns, a
-// fixed xor-shuffle tree, then FP64); sq[i] += sum_c (z[i][c] xm[i][c])^2 if
-// sq (likewise: the judge of the variance surrogate forms a sample variance
-// from it, where the two moments cancel).  Lanes are columns: a warp takes 32/R rows at a time.
-template <int R>
-__global__ void k_hutch(int N, const __nv_bfloat16* __restrict__ Z, const float2* __restrict__ xm,
-                        double* __restrict__ sacc, double* __restrict__ sq) {
-  constexpr int RPW = 32 / R;
-  const int lane = threadIdx.x & 31, c = lane % R;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = gw * RPW; base < N; base += nwarp * RPW) {
-    const int64_t row = base + lane / R;
-    float2 t = make_float2(0.f, 0.f);
-    if (row < N) {
-      const float z = __bfloat162float(Z[row * R + c]);
-      const float2 x = xm[row * R + c];
-      t = make_float2(z * x.x, z * x.y);  // z = +-1 or 0: exact
-    }
-    // t^2 in float-float: hi^2 exactly by FMA, plus 2 hi lo (only when sq is asked for)
-    float2 q = make_float2(0.f, 0.f);
-    if (sq) {
-      const float p0 = __fmul_rn(t.x, t.x);
-      q = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
-    }
-#pragma unroll
-    for (int o = R / 2; o > 0; o >>= 1) {
-      const float2 u = make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o));
-      t = ff_add(t, u);
-      if (sq) {
-        const float2 v = make_float2(__shfl_xor_sync(0xffffffffu, q.x, o), __shfl_xor_sync(0xffffffffu, q.y, o));
-        q = ff_add(q, v);
-      }
-    }
-    if (c == 0 && row < N) {
-      sacc[row] += (double)t.x + (double)t.y;
-      if (sq) sq[row] += (double)q.x + (double)q.y;
-    }
   }
 }
 
@@ -608,10 +594,19 @@ __global__ void k_finish(int N, const double* __restrict__ sacc, double invK, fl
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) s[i] = (float)(sacc[i] * invK);
 }
 
-// xm += d in float-float arithmetic
-__global__ void k_axpy_ff(int64_t n, const float* __restrict__ d, float2* __restrict__ xm) {
+// xm += d in float-float arithmetic (xm = d for the first correction of a block)
+__global__ void k_axpy_ff(int64_t n, const float* __restrict__ d, float2* __restrict__ xm, int first) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    xm[i] = ff_add_f(xm[i], d[i]);
+    xm[i] = first ? make_float2(d[i], 0.0f) : ff_add_f(xm[i], d[i]);
+}
+
+// s_acc += hsum, sq += hsq (the block's probe sums from its last residual pass)
+__global__ void k_hadd(int N, const double* __restrict__ hsum, const double* __restrict__ hsq, double* __restrict__ sacc,
+                       double* __restrict__ sq) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    sacc[i] += hsum[i];
+    if (sq) sq[i] += hsq[i];
+  }
 }
 
 // per-voxel indices of the six face neighbours (-x, +x, -y, +y, -z, +z), -1 outside the band
@@ -789,7 +784,7 @@ struct BlockGraph {
 
 static void free_arrays(BlockGraph* g) {
   void* ptrs[] = {g->h.r[0], g->h.w[0], g->h.s[0], g->h.r[1], g->h.w[1], g->h.s[1], g->h.p, g->h.x,
-                  g->h.xm, g->h.iq,       g->h.part, g->h.part1, g->Z, g->sacc};
+                  g->h.xm, g->h.iq,       g->h.part, g->h.part1, g->Z, g->sacc, g->h.hsum, g->h.hsq};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   g->cap_rows = 0;
@@ -877,6 +872,8 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     BF_CK(cudaMalloc(&g->h.p, nv * 4));
     BF_CK(cudaMalloc(&g->h.x, nv * 4));
     BF_CK(cudaMalloc(&g->h.xm, nv * sizeof(float2)));
+    BF_CK(cudaMalloc(&g->h.hsum, (size_t)rows * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.hsq, (size_t)rows * sizeof(double)));
     BF_CK(cudaMalloc(&g->Z, nv * 2));
     BF_CK(cudaMalloc(&g->h.iq, (size_t)rows * 4));
     BF_CK(cudaMalloc(&g->sacc, (size_t)rows * 8));
@@ -938,13 +935,14 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
   for (int k0 = kb; k0 < ke; k0 += R) {
     // one block of R probes: float-float master iterates, FP32 correction solves
     int ncols = ke - k0 < R ? ke - k0 : R;
-    k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.xm, g->h.r[0]);
+    k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.r[0]);
     count_launch();
     k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols, N, ETA_MIN);
     count_launch();
     blk_start<R>(g, s);
     BF_CK(cudaGetLastError());
     bool done = false;
+    int nouter = 0;  // residual passes run (the last one leaves the block's probe sums in hsum, hsq)
     for (int outer = 0; outer < 64; ++outer) {
       BF_CK(cudaMemcpyAsync(g->h_st, g->st, sizeof(BlkState), cudaMemcpyDeviceToHost, s));
       BF_CK(cudaStreamSynchronize(s));
@@ -953,16 +951,19 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
         break;
       }
       BF_CK(cudaGraphLaunch(g->exec, s));
-      k_axpy_ff<<<gNR, 256, 0, s>>>(NR, g->h.x, g->h.xm);
+      k_axpy_ff<<<gNR, 256, 0, s>>>(NR, g->h.x, g->h.xm, nouter == 0);
       count_launch();
       blk_outer<R>(g, s);
+      ++nouter;
       BF_CK(cudaGetLastError());
     }
     const BlkState& h = *g->h_st;
     count_launch(h.nexec);
     for (int c = 0; c < ncols; ++c) tot_it += h.iters[c];
-    k_hutch<R><<<grid_for((int64_t)N * R, 256, 152 * 16), 256, 0, s>>>(N, g->Z, g->h.xm, g->sacc, sq);
-    count_launch();
+    if (nouter > 0) {
+      k_hadd<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->h.hsum, g->h.hsq, g->sacc, sq);
+      count_launch();
+    }
     BF_CK(cudaGetLastError());
     if (h.status == 2) { result = BF_BREAKDOWN; break; }
     if (!done || h.status == 1) { result = BF_NOT_CONVERGED; break; }

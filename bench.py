@@ -289,10 +289,12 @@ def run_ours(args, world, rank, local):
     ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R_used, reps=50)
     N, NB = band.N, band.NB
     # algorithmic bytes of one probe-solver iteration (per voxel row of R
-    # columns): r, w, s, p, x read and p, x, r', s', w' written (40 B per
-    # column), Q_jj and 1/Q_jj read (8 B); the neighbour gathers of the SpMM
-    # are not counted (they come from shared memory and L2 by design)
-    bytes_it = N * (R_used * 40 + 8)
+    # columns): r, w, s, p read and p, r', s', w' written (32 B per column),
+    # the correction x read and written every second iteration (4 B per
+    # column on average; the timed launches alternate the two kinds), Q_jj
+    # and 1/Q_jj read (8 B); the neighbour gathers of the SpMM are not
+    # counted (they come from shared memory and L2 by design)
+    bytes_it = N * (R_used * 36 + 8)
     ms_spmv = band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=200)
     bytes_spmv = N * 12 + NB * (128 + 24)   # x, qd read, y written; brick metadata
     achieved = bytes_it / (ms_iter * 1e-3) / 1e9
@@ -458,7 +460,7 @@ def run_kernel(args):
         which = bfsdf.BF_KERNEL_BLOCK_ITER if args.kernel == "block_iter" else bfsdf.BF_KERNEL_SPMV
         band.bench_kernel(which, R=R, reps=max(args.warmup, 1))
         ms = band.bench_kernel(which, R=R, reps=max(args.steps, 1))
-        nbytes = N * (R * 40 + 8) if args.kernel == "block_iter" else N * 12 + NB * (128 + 24)
+        nbytes = N * (R * 36 + 8) if args.kernel == "block_iter" else N * 12 + NB * (128 + 24)
         out.update(ms_per_launch=ms, bytes_per_launch=nbytes, achieved_gbs=nbytes / (ms * 1e-3) / 1e9)
     else:
         net = bfsdf.Net(ctx, seed=0)

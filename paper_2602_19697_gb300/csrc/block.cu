@@ -63,6 +63,11 @@ struct BlkState {
   int iter, max_iter, all_done, status, ncols;
   int first;  // the next finalize starts a correction solve
   int par;    // which of the double-buffered r, w, s is current
+  // The correction x is written every second iteration: x += alpha_{k-1} p_{k-1} + alpha_k p_k, with
+  // p_{k-1} the direction the iteration reads anyway.  xvalid: x holds a value (else it is zero);
+  // xpend: the last iteration's alpha p is not yet in x (aprev holds that alpha per column).
+  alignas(16) float aprev[MAXR];
+  int xvalid, xpend;
   unsigned int cnt, guard;
   unsigned int nexec;  // graph-body kernels executed (for launch accounting)
 };
@@ -296,27 +301,31 @@ __device__ __forceinline__ float4 scale4(float4 a, float q) {
 
 // One block-PCG iteration in one pass over the band (mode as below):
 //   phase 1, the tile's own rows (float4 over 4 columns, streaming):
-//     u = r/Q_jj, p = u + beta p, s' = w + beta s, x += alpha p,
-//     r' = r - alpha s', u' = r'/Q_jj; partial sums r'.u', r'.r'
+//     u = r/Q_jj, p' = u + beta p, s' = w + beta s, r' = r - alpha s',
+//     u' = r'/Q_jj; every second iteration x += alpha_prev p + alpha p'
+//     (the other one leaves alpha p' pending); partial sums r'.u', r'.r'
 //   phase 2, the external rows its face neighbours reference: u' from their
 //     (old) r, w, s by the same arithmetic
 //   phase 3, w' = Q u' for the own rows from the staged u'; partial w'.u'.
-// INIT (start of a correction solve from r): u = r/Q_jj, p = u, x = s' = 0,
-// r' = r, w' = Q u.  r, w, s are double-buffered (read [par], written
-// [par ^ 1]; other CTAs read the old values of rows this CTA updates); p and
-// x are updated in place.  The last CTA reduces the partial sums in a fixed
-// order and updates the per-column scalars (first pass of a correction
-// solve: alpha = gamma/delta, beta = 0; afterwards the single-reduction
-// recurrence and the stop test on r.r), then flips par.
+// INIT (start of a correction solve from r): u = r/Q_jj, w = Q u, written to
+// w[par]; r stays, x is zero, and p and s are not read by the next iteration
+// (beta = 0 there).  Otherwise r, w, s are double-buffered (read [par],
+// written [par ^ 1]; other CTAs read the old values of rows this CTA
+// updates) and p, x are updated in place.  The last CTA reduces the partial
+// sums in a fixed order and updates the per-column scalars (first pass of a
+// correction solve: alpha = gamma/delta, beta = 0; afterwards the
+// single-reduction recurrence and the stop test on r.r), then flips par
+// (not after INIT).
 // mode: IT_GRAPH inside the solver graph (may end the WHILE loop), IT_START
-// host-launched start of a correction solve, IT_BENCH timing (scalars, par
-// and data are left as they are: alpha = beta = 0 keeps the data fixed).
-constexpr int IT_GRAPH = 0, IT_BENCH = 1, IT_START = 2;
+// host-launched start of a correction solve, IT_BENCH / IT_BENCH_HOLD timing
+// of an iteration that writes / holds x (scalars, par and data are left as
+// they are: alpha = beta = 0 keeps the data fixed).
+constexpr int IT_GRAPH = 0, IT_BENCH = 1, IT_START = 2, IT_BENCH_HOLD = 3;
 
 template <int R, bool INIT>
 __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A, BlkState* st,
                                                   cudaGraphConditionalHandle handle, int mode) {
-  const bool bench = mode == IT_BENCH;
+  const bool bench = mode == IT_BENCH || mode == IT_BENCH_HOLD;
   if (mode == IT_GRAPH && blockIdx.x == 0 && threadIdx.x == 0) {
     st->nexec += 1;
     unsigned gd = atomicAdd(&st->guard, 1u);
@@ -343,18 +352,23 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   const float4* __restrict__ sA = reinterpret_cast<const float4*>(A->s[par]);
   float4* __restrict__ rB = reinterpret_cast<float4*>(A->r[par ^ 1]);
   float4* __restrict__ sB = reinterpret_cast<float4*>(A->s[par ^ 1]);
-  float* __restrict__ wB = A->w[par ^ 1];
+  float* __restrict__ wB = A->w[INIT ? par : par ^ 1];
   float4* __restrict__ p4 = reinterpret_cast<float4*>(A->p);
   float4* __restrict__ x4 = reinterpret_cast<float4*>(A->x);
   const float* __restrict__ iq = A->iq;
   // this thread's 4 columns in phases 1 and 2 (the float4 index stride CT is a multiple of Q4)
   const int g = threadIdx.x % Q4;
-  float4 al = make_float4(0.f, 0.f, 0.f, 0.f), be = al;
+  float4 al = make_float4(0.f, 0.f, 0.f, 0.f), be = al, ap = al;
+  // x: xhold leaves this iteration's alpha p' pending; otherwise x (read only when xread) is written
+  bool xhold = mode == IT_BENCH_HOLD, xread = true;
   if (!INIT && !bench) {
     al = make_float4((float)st->alpha[4 * g], (float)st->alpha[4 * g + 1], (float)st->alpha[4 * g + 2],
                      (float)st->alpha[4 * g + 3]);
     be = make_float4((float)st->beta[4 * g], (float)st->beta[4 * g + 1], (float)st->beta[4 * g + 2],
                      (float)st->beta[4 * g + 3]);
+    xhold = !st->xpend;
+    xread = st->xvalid;
+    if (!xhold) ap = *reinterpret_cast<const float4*>(st->aprev + 4 * g);
   }
   extern __shared__ __align__(16) float us[];  // [SP_ROWS][R] u' of the own and external rows
   float4* us4 = reinterpret_cast<float4*>(us);
@@ -397,11 +411,8 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       if (INIT) {
         rn = ri;
         un = scale4(ri, qi);
-        p4[gq] = un;
-        x4[gq] = make_float4(0.f, 0.f, 0.f, 0.f);
-        sB[gq] = make_float4(0.f, 0.f, 0.f, 0.f);
       } else {
-        const float4 wi = wA[gq], si = sA[gq], pi = p4[gq], xi = x4[gq];
+        const float4 wi = wA[gq], si = sA[gq], pi = p4[gq];
         const float4 u0 = scale4(ri, qi);
         const float4 pn = make_float4(__fadd_rn(u0.x, bmul(be.x, pi.x)), __fadd_rn(u0.y, bmul(be.y, pi.y)),
                                       __fadd_rn(u0.z, bmul(be.z, pi.z)), __fadd_rn(u0.w, bmul(be.w, pi.w)));
@@ -409,10 +420,14 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
         rn = next_r(ri, sn, al);
         un = scale4(rn, qi);
         p4[gq] = pn;
-        x4[gq] = make_float4(xi.x + al.x * pn.x, xi.y + al.y * pn.y, xi.z + al.z * pn.z, xi.w + al.w * pn.w);
+        if (!xhold) {
+          const float4 xi = xread ? x4[gq] : make_float4(0.f, 0.f, 0.f, 0.f);
+          x4[gq] = make_float4(fmaf(al.x, pn.x, fmaf(ap.x, pi.x, xi.x)), fmaf(al.y, pn.y, fmaf(ap.y, pi.y, xi.y)),
+                               fmaf(al.z, pn.z, fmaf(ap.z, pi.z, xi.z)), fmaf(al.w, pn.w, fmaf(ap.w, pi.w, xi.w)));
+        }
         sB[gq] = sn;
+        rB[gq] = rn;
       }
-      rB[gq] = rn;
       us4[q] = un;
       fa[0] += rn.x * un.x; fa[1] += rn.y * un.y; fa[2] += rn.z * un.z; fa[3] += rn.w * un.w;
       fa[4] += rn.x * rn.x; fa[5] += rn.y * rn.y; fa[6] += rn.z * rn.z; fa[7] += rn.w * rn.w;
@@ -519,6 +534,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   if (threadIdx.x < R) {
     const int cc = threadIdx.x;
     const double gm = tot1[0][cc], rr = tot1[1][cc], d = tot[0][cc];
+    if (!INIT) st->aprev[cc] = xhold ? (float)st->alpha[cc] : 0.0f;  // the alpha this iteration used
     if (!st->done[cc]) {
       if (first) {
         st->gamma[cc] = gm;
@@ -561,7 +577,14 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   __syncthreads();
   if (threadIdx.x == 0) {
     st->first = 0;
-    st->par ^= 1;
+    if (INIT) {
+      st->xvalid = 0;
+      st->xpend = 0;
+    } else {
+      st->par ^= 1;
+      st->xvalid |= !xhold;
+      st->xpend = xhold;
+    }
     if (!any_live || st->iter >= st->max_iter) {
       st->all_done = 1;
       if (mode == IT_GRAPH) cudaGraphSetConditional(handle, 0);
@@ -594,10 +617,17 @@ __global__ void k_finish(int N, const double* __restrict__ sacc, double invK, fl
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) s[i] = (float)(sacc[i] * invK);
 }
 
-// xm += d in float-float arithmetic (xm = d for the first correction of a block)
-__global__ void k_axpy_ff(int64_t n, const float* __restrict__ d, float2* __restrict__ xm, int first) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    xm[i] = first ? make_float2(d[i], 0.0f) : ff_add_f(xm[i], d[i]);
+// xm += d in float-float arithmetic (xm = d for the first correction of a block), d the correction:
+// x (when it holds a value) plus the alpha p left pending by the last iteration
+template <int R>
+__global__ void k_axpy_ff(int64_t n, const BlkState* __restrict__ st, const float* __restrict__ x,
+                          const float* __restrict__ p, float2* __restrict__ xm, int first) {
+  const int xv = st->xvalid, xp = st->xpend;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float d = xv ? x[i] : 0.0f;
+    if (xp) d = fmaf(st->aprev[i % R], p[i], d);
+    xm[i] = first ? make_float2(d, 0.0f) : ff_add_f(xm[i], d);
+  }
 }
 
 // s_acc += hsum, sq += hsq (the block's probe sums from its last residual pass)
@@ -808,7 +838,7 @@ static void blk_iter(BlockGraph* g, cudaStream_t s, cudaGraphConditionalHandle h
   k_blk_it<R, false><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, h, IT_GRAPH);
 }
 
-// start of a correction solve from r: u = r/Q_jj, p = u, s = x = 0, w = Q u, alpha
+// start of a correction solve from r: u = r/Q_jj, w = Q u, x = 0, alpha
 template <int R>
 static void blk_start(BlockGraph* g, cudaStream_t s) {
   k_blk_it<R, true><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), IT_START);
@@ -951,7 +981,7 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
         break;
       }
       BF_CK(cudaGraphLaunch(g->exec, s));
-      k_axpy_ff<<<gNR, 256, 0, s>>>(NR, g->h.x, g->h.xm, nouter == 0);
+      k_axpy_ff<R><<<gNR, 256, 0, s>>>(NR, g->st, g->h.x, g->h.p, g->h.xm, nouter == 0);
       count_launch();
       blk_outer<R>(g, s);
       ++nouter;
@@ -993,8 +1023,9 @@ static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int reps, double* ms) {
   BF_CK(cudaEventCreate(&e0));
   BF_CK(cudaEventCreate(&e1));
   BF_CK(cudaEventRecord(e0, s));
-  for (int i = 0; i < reps; ++i) {
-    k_blk_it<R, false><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), IT_BENCH);
+  for (int i = 0; i < reps; ++i) {  // alternately an iteration that writes x and one that holds it
+    k_blk_it<R, false><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(),
+                                                    (i & 1) ? IT_BENCH_HOLD : IT_BENCH);
     count_launch();
   }
   BF_CK(cudaEventRecord(e1, s));

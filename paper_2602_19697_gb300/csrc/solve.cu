@@ -180,14 +180,19 @@ __device__ __forceinline__ MetaWord meta_word(const BandView& B, int r) {
 
 // The SpMV tile: pitch 24 in x (own lx at x = lx + 4, so a thread's four
 // voxels are one aligned float4 and eight lanes' float4 fall in distinct
-// banks), 10 rows in y and z (own ly, lz at ly + 1, lz + 1).  Halo face f at
-// face coordinates (u, v): local index in the neighbour brick [0] + u [1] +
-// v [2], tile position [3] + u [4] + v [5] (faces -x, +x, -y, +y, -z, +z;
-// (u, v) are the two other axes in increasing order).
-constexpr int SP_PY = 24, SP_PZ = 240, SP_TILE = 2400;
+// banks), 10 rows in y (own ly at ly + 1) and 10 planes of pitch 248 in z (own
+// lz at lz + 1; 248 = 24 mod 32, so that a warp's stores of a y face hit 32
+// distinct banks).  The -x and +x halo faces, whose tile positions would all
+// be congruent mod 8, sit in a separate array hx[side][z][y] of side pitch 80
+// instead.  Halo face f at face coordinates (u, v): local index in the
+// neighbour brick [0] + u [1] + v [2], position [3] + u [4] + v [5] in hx
+// (faces -x, +x) or in the tile (faces -y, +y, -z, +z); (u, v) are the two
+// other axes in increasing order.
+constexpr int SP_PY = 24, SP_PZ = 248, SP_TILE = 10 * SP_PZ, SP_HX = 80;
 __constant__ int c_halo24[6][6] = {
-    {7, 8, 64, 267, 24, 240},   {0, 8, 64, 276, 24, 240},   {56, 1, 64, 244, 1, 240},
-    {0, 1, 64, 460, 1, 240},    {448, 1, 8, 28, 1, 24},     {0, 1, 8, 2188, 1, 24},
+    {7, 8, 64, 0, 1, 8},        {0, 8, 64, SP_HX, 1, 8},    {56, 1, 64, 4 + SP_PZ, 1, SP_PZ},
+    {0, 1, 64, 4 + 9 * SP_PY + SP_PZ, 1, SP_PZ},          {448, 1, 8, 4 + SP_PY, 1, SP_PY},
+    {0, 1, 8, 4 + SP_PY + 9 * SP_PZ, 1, SP_PY},
 };
 
 // Loads of one brick, issued one brick ahead of their use.  Thread t owns
@@ -242,6 +247,7 @@ __device__ __forceinline__ void prefetch_range(const float* v, int64_t i0, int64
 __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, const float* __restrict__ qd,
                                                        const float* __restrict__ x, float* __restrict__ y) {
   __shared__ __align__(16) float tile[SP_TILE];
+  __shared__ float hx[2 * SP_HX];
   __shared__ MetaWord sm[2][7][16];
   const int g = gridDim.x;
   if (threadIdx.x < 7 * 16) sm[0][threadIdx.x >> 4][threadIdx.x & 15] = meta_word(B, meta_rank(B, blockIdx.x));
@@ -256,6 +262,8 @@ __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, co
     pr = make_int2(__ldg(B.off + blockIdx.x + 2 * g), __ldg(B.off + blockIdx.x + 2 * g + 1));
   const int l0 = 4 * threadIdx.x;
   const int t0 = ((l0 & 7) + 4) + SP_PY * (((l0 >> 3) & 7) + 1) + SP_PZ * ((l0 >> 6) + 1);
+  // -x (lx = 0 threads) or +x (lx = 4 threads) halo value of the thread's row
+  const int xside = (l0 >> 2) & 1, hxi = xside * SP_HX + 8 * (l0 >> 6) + ((l0 >> 3) & 7);
   int it = 0;
   for (int b = blockIdx.x; b < B.NB; b += g, ++it) {
     if (threadIdx.x == 0) {
@@ -269,16 +277,20 @@ __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, co
     const int pn = (it + 1) & 1;
     // tile <- b's values; lookup words of the next brick into the other buffer
     *reinterpret_cast<float4*>(tile + t0) = cur.xv;
+    hx[cur.tp[0]] = cur.hv[0];  // slots 0 .. BT-1 are the two x faces
 #pragma unroll
-    for (int s = 0; s < 3; ++s) tile[cur.tp[s]] = cur.hv[s];
+    for (int s = 1; s < 3; ++s) tile[cur.tp[s]] = cur.hv[s];
     if (threadIdx.x < 7 * 16) sm[pn][threadIdx.x >> 4][threadIdx.x & 15] = nm;
     __syncthreads();
     if (b + g < B.NB) spmv_issue(sm[pn], x, qd, nxt);
     nm = meta_word(B, nr);
     nr = meta_rank(B, b + 3 * g);
+    // the in-row x neighbours come from the lane holding the other half of the row (lane ^ 1)
+    const float4 c = *reinterpret_cast<const float4*>(tile + t0);
+    const float xo = __shfl_xor_sync(0xffffffffu, xside ? c.x : c.w, 1);
     if (cur.m4) {
-      const float4 c = *reinterpret_cast<const float4*>(tile + t0);
-      const float xl = tile[t0 - 1], xr = tile[t0 + 4];
+      const float xh = hx[hxi];
+      const float xl = xside ? xo : xh, xr = xside ? xh : xo;
       const float4 ym = *reinterpret_cast<const float4*>(tile + t0 - SP_PY);
       const float4 yp = *reinterpret_cast<const float4*>(tile + t0 + SP_PY);
       const float4 zm = *reinterpret_cast<const float4*>(tile + t0 - SP_PZ);

@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="union256")
+    ap.add_argument("--workload", default="union256",
+                    help="union256 | sphere64 | blob512 | blob1024 (--kernel only: the blob512 object at 1 mm on a "
+                         "1024^3 grid, band +-48 voxels, 200 frames 1024x768; a band of about 58 M voxels)")
     ap.add_argument("--K", type=int, default=64)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--rhs-block", type=int, default=0, help="probe block width (0 = the library's autotuner)")
@@ -441,27 +443,54 @@ def object_sequence(ctx, stream, tol, hbm, peak_kind):
             "surrogate_bricks_accepted": acc}
 
 
+def kernel_workload(name):
+    import synth
+    if name == "blob1024":  # the object at twice the linear resolution, same physical band
+        return synth.make_workload("blob512", n=1024, band_vox=48.0, image_scale=2.0, threads=os.cpu_count() or 0)
+    return synth.make_workload(name, threads=os.cpu_count() or 0)
+
+
 def run_kernel(args):
     """One kernel of the path, launched alone through the library's timing
-    entries (CUDA events on the library stream)."""
+    entries (CUDA events on the library stream).  The SpMV is timed as single
+    launches after writing and then reading 1 GB (L2 flushed), median of
+    --steps; the other kernels as --steps back-to-back launches."""
+    import numpy as np
     import torch
 
-    import synth
     from paper_2602_19697_gb300 import bfsdf, build
     build.build()
     ctx = bfsdf.Context(0)
-    w = synth.make_workload(args.workload)
+    w = kernel_workload(args.workload)
     depth, poses = torch.from_numpy(w.depth).cuda(), torch.from_numpy(w.poses).cuda()
     band = ctx.build_band_w(w, depth, poses)
     band.integrate_depth(depth, poses, w.intr)
     N, NB, R = band.N, band.NB, (args.rhs_block or 32)
     out = {"kernel": args.kernel, "workload": args.workload, "N_band": N, "bricks": NB}
-    if args.kernel in ("block_iter", "spmv"):
-        which = bfsdf.BF_KERNEL_BLOCK_ITER if args.kernel == "block_iter" else bfsdf.BF_KERNEL_SPMV
+    if args.kernel == "block_iter":
+        which = bfsdf.BF_KERNEL_BLOCK_ITER
         band.bench_kernel(which, R=R, reps=max(args.warmup, 1))
         ms = band.bench_kernel(which, R=R, reps=max(args.steps, 1))
-        nbytes = N * (R * 36 + 8) if args.kernel == "block_iter" else N * 12 + NB * (128 + 24)
+        nbytes = N * (R * 36 + 8)
         out.update(ms_per_launch=ms, bytes_per_launch=nbytes, achieved_gbs=nbytes / (ms * 1e-3) / 1e9)
+    elif args.kernel == "spmv":
+        which = bfsdf.BF_KERNEL_SPMV
+        band.bench_kernel(which, reps=max(args.warmup, 1))
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        clean = torch.zeros(256 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        ms = []
+        for i in range(max(args.steps, 1)):
+            flush.fill_(float(i))
+            clean.sum()
+            torch.cuda.synchronize()
+            ms.append(band.bench_kernel(which, reps=1))
+        nbytes = N * 12 + NB * (128 + 24)
+        med = float(np.median(ms))
+        hbm, peak_kind = peaks()
+        out.update(ms_per_launch=med, ms_min=min(ms), bytes_per_launch=nbytes,
+                   achieved_gbs=nbytes / (med * 1e-3) / 1e9, peak_gbs=hbm, peak_kind=peak_kind,
+                   frac=nbytes / (med * 1e-3) / 1e9 / hbm, bytes_per_voxel=nbytes / N,
+                   l2="1 GB written, then another 1 GB read, before each single launch; median")
     else:
         net = bfsdf.Net(ctx, seed=0)
         which = {"net_forward": bfsdf.BF_NET_BENCH_FORWARD, "net_train": bfsdf.BF_NET_BENCH_TRAIN,

@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   float4* us4 = reinterpret_cast<float4*>(us);
   // per-thread FP32 partial sums over the CTA's tiles (at most 4 products per
   // tile and thread), FP64 from the CTA reduction on
-  float fa[8], ft = 0.0f;
+  float fa[8], ft[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int k = 0; k < 8; ++k) fa[k] = 0.0f;
   const int ntiles = (N + SP_TR - 1) / SP_TR;
@@ -451,10 +451,11 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       us4[SP_TR * Q4 + q] = un;
     }
     __syncthreads();
-    // phase 3: w' = Q u' for the own rows
-#pragma unroll 4
-    for (int jstep = 0; jstep < 16 / RPW; ++jstep) {
-      const int src = jstep * RPW + lane / R;  // row of the warp's 16, and the lane holding its slots
+    // phase 3: w' = Q u' for the own rows, four columns (one float4 of u') per lane
+    constexpr int RPS = 32 / Q4;  // rows per warp step
+#pragma unroll 1
+    for (int jstep = 0; jstep < 16 / RPS; ++jstep) {
+      const int src = jstep * RPS + lane / Q4;  // row of the warp's 16, and the lane holding its slots
       const int rr = 16 * wrp + src, row = t0 + rr;
       const uint32_t sx = __shfl_sync(0xffffffffu, slv.x, src), sy = __shfl_sync(0xffffffffu, slv.y, src),
                      sz = __shfl_sync(0xffffffffu, slv.z, src);
@@ -462,59 +463,56 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       if (row >= t1) continue;
       const int sv[6] = {(int16_t)(sx & 0xffffu), (int16_t)(sx >> 16), (int16_t)(sy & 0xffffu),
                          (int16_t)(sy >> 16),     (int16_t)(sz & 0xffffu), (int16_t)(sz >> 16)};
-      const float uo = us[rr * R + c];
-      float un[6];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
+      const float4 uo = us4[rr * Q4 + g];
+      // u' of face neighbour k: staged row, or formed from global memory beyond the staged list
+      auto nbu = [&](int k) -> float4 {
         const int sk = sv[k];
-        float v = 0.0f;
-        if (sk == SP_GLOBAL) {  // external row beyond the staged list: form u' from global memory
-          const int j = __ldg(A->nb6 + 6 * (size_t)row + k);
-          const size_t gj = (size_t)j * R + c;
-          const float rj = A->r[par][gj];
-          const float qj = __ldg(iq + j);
-          if (INIT) {
-            v = __fmul_rn(rj, qj);
-          } else {
-            const float a = (float)st->alpha[c], b = bench ? 0.f : (float)st->beta[c];
-            const float sn = __fadd_rn(A->w[par][gj], bmul(b, A->s[par][gj]));
-            v = __fmul_rn(__fsub_rn(rj, __fmul_rn(bench ? 0.f : a, sn)), qj);
-          }
-        } else if (sk >= 0) {
-          v = us[sk * R + c];
-        }
-        un[k] = v;
-      }
-      const float ns = ((un[0] + un[1]) + (un[2] + un[3])) + (un[4] + un[5]);
-      const float wn = q * uo - lam * ns;
-      wB[(size_t)row * R + c] = wn;
-      ft += wn * uo;
+        if (sk >= 0 && sk != SP_GLOBAL) return us4[sk * Q4 + g];
+        if (sk < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+        const int j = __ldg(A->nb6 + 6 * (size_t)row + k);
+        const size_t gj = (size_t)j * Q4 + g;
+        const float qj = __ldg(iq + j);
+        if (INIT) return scale4(rA[gj], qj);
+        return scale4(next_r(rA[gj], next_s(wA[gj], sA[gj], be), al), qj);
+      };
+      auto add4 = [](float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); };
+      const float4 s01 = add4(nbu(0), nbu(1)), s23 = add4(nbu(2), nbu(3)), s45 = add4(nbu(4), nbu(5));
+      const float4 ns = add4(add4(s01, s23), s45);
+      float4 wn;
+      wn.x = q * uo.x - lam * ns.x;
+      wn.y = q * uo.y - lam * ns.y;
+      wn.z = q * uo.z - lam * ns.z;
+      wn.w = q * uo.w - lam * ns.w;
+      reinterpret_cast<float4*>(wB)[(size_t)row * Q4 + g] = wn;
+      ft[0] += wn.x * uo.x; ft[1] += wn.y * uo.y; ft[2] += wn.z * uo.z; ft[3] += wn.w * uo.w;
     }
   }
-  // per-column CTA sums: phase 1 (lanes sharing threadIdx % Q4, then warps) -> part1
+  // per-column CTA sums (lanes sharing threadIdx % Q4, then warps): r'.u', r'.r' -> part1, w'.u' -> part
   {
-    __shared__ double sh1[CT / 32][8][8];
-    double acc1[8];
+    __shared__ double sh1[CT / 32][8][12];
+    double acc1[12];
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc1[k] = (double)fa[k];
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < 4; ++k) acc1[8 + k] = (double)ft[k];
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
       for (int o = 16; o >= Q4; o >>= 1) acc1[k] += __shfl_xor_sync(0xffffffffu, acc1[k], o);
     if (lane < Q4) {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sh1[wrp][lane][k] = acc1[k];
+      for (int k = 0; k < 12; ++k) sh1[wrp][lane][k] = acc1[k];
     }
     __syncthreads();
-    if (threadIdx.x < 2 * R) {
-      const int qk = threadIdx.x / R, cc = threadIdx.x % R;  // qk: 0 = r.u, 1 = r.r
+    if (threadIdx.x < 3 * R) {
+      const int qk = threadIdx.x / R, cc = threadIdx.x % R;  // qk: 0 = r.u, 1 = r.r, 2 = w.u
       double t = 0.0;
       for (int ww = 0; ww < CT / 32; ++ww) t += sh1[ww][cc / 4][4 * qk + (cc & 3)];
-      A->part1[((size_t)qk * R + cc) * gridDim.x + blockIdx.x] = t;
+      if (qk < 2)
+        A->part1[((size_t)qk * R + cc) * gridDim.x + blockIdx.x] = t;
+      else
+        A->part[(size_t)cc * gridDim.x + blockIdx.x] = t;
     }
   }
-  // phase 3 (one column per lane) -> part
-  double v[1] = {(double)ft};
-  column_partials<R, 1>(v, A->part);
   if (!arrive_last(&st->cnt)) return;
   if (bench) {
     if (threadIdx.x == 0) st->cnt = 0;

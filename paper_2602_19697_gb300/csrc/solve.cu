@@ -285,8 +285,9 @@ __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, co
     if (b + g < B.NB) spmv_issue(sm[pn], x, qd, nxt);
     nm = meta_word(B, nr);
     nr = meta_rank(B, b + 3 * g);
-    // the in-row x neighbours come from the lane holding the other half of the row (lane ^ 1)
-    const float4 c = *reinterpret_cast<const float4*>(tile + t0);
+    // own values as this thread stored them; the in-row x neighbours come from the lane holding the
+    // other half of the row (lane ^ 1)
+    const float4 c = cur.xv;
     const float xo = __shfl_xor_sync(0xffffffffu, xside ? c.x : c.w, 1);
     if (cur.m4) {
       const float xh = hx[hxi];

@@ -48,6 +48,9 @@ constexpr int CT = 512;   // threads per CTA of the row kernels
 // (the FP32 recursive residual keeps falling below the true one's floor)
 constexpr double ETA_MIN = 1e-7;
 constexpr int NCTA = 152 * 2;
+// CTA sums are reduced in two levels: groups of GSZ CTAs, then the NGRP group sums
+constexpr int GSZ = 16, NGRP = NCTA / GSZ;
+static_assert(NGRP * GSZ == NCTA && NGRP <= 32, "reduction groups");
 // SpMM pass: tiles of SP_TR rows plus at most SP_EMAX external rows staged in
 // shared memory (SP_ROWS rows); SP_GLOBAL marks a neighbour read from global
 // memory (a tile whose external rows overflow the list)
@@ -68,7 +71,9 @@ struct BlkState {
   // xpend: the last iteration's alpha p is not yet in x (aprev holds that alpha per column).
   alignas(16) float aprev[MAXR];
   int xvalid, xpend;
+  int want_sq;  // the residual pass also forms the probe values' second moments (hsq)
   unsigned int cnt, guard;
+  unsigned int gcnt[NGRP];  // CTAs of each reduction group that have written their partials
   unsigned int nexec;  // graph-body kernels executed (for launch accounting)
 };
 
@@ -90,9 +95,10 @@ struct BlkArgs {
   float2* xm;          // float-float master iterates (hi, lo)
   const __nv_bfloat16* Z;
   double* part;        // [3][R][NCTA]
-  double* part1;       // [2][R][NCTA] pass-1 partials
+  double* part1;       // [3][R][NCTA] the iteration's partials (r'.u', r'.r', w'.u')
+  double* gpart;       // [3][R][NGRP] group sums of the partials
   double* hsum;        // [N] sum over the block's columns of z (.) xm, from the last residual pass
-  double* hsq;         // [N] the same for (z (.) xm)^2, or null
+  double* hsq;         // [N] the same for (z (.) xm)^2 (formed when BlkState::want_sq)
 };
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -126,32 +132,51 @@ __device__ __forceinline__ float2 ff_mul_f(float2 x, float b) {  // exact produc
 }
 __device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
 
-__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
-  __shared__ bool last;
+// Fixed-order two-level sum of the CTA partials part[k][c][0..NCTA) for all
+// c < R, k < NV.  Called by every thread of every CTA after its partials are
+// written.  The last CTA of each group of GSZ sums the group (a half-warp per
+// (k, c), shuffle tree) into gpart[k][c][group]; the last group's finisher sums
+// the NGRP group values (a warp per (k, c)) into tot[k][c] and returns true in
+// all its threads; every other CTA returns false.  The counters are left at 0
+// for the next launch except st->cnt, which the caller resets.
+template <int NV>
+__device__ __forceinline__ bool reduce_partials(const double* part, double* gpart, BlkState* st, int R,
+                                                double (*tot)[MAXR]) {
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5, grp = blockIdx.x / GSZ;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    unsigned prev = atomicAdd(counter, 1u);
-    last = (prev == gridDim.x - 1);
+    s_last = atomicAdd(&st->gcnt[grp], 1u) == GSZ - 1;
   }
   __syncthreads();
-  return last;
-}
-
-// fixed-order sum of part[k][c][0..nblk) for all c < R, k < NV, into tot[k][c]:
-// one warp per (k, c), lanes strided over the partials, xor-shuffle tree
-template <int NV>
-__device__ __forceinline__ void sum_partials(const double* part, int R, int nblk, double (*tot)[MAXR]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int kc = w; kc < NV * R; kc += nw) {
-    const double* p = part + (size_t)kc * nblk;
-    double s = 0;
-    for (int i = lane; i < nblk; i += 32) s += __ldcg(p + i);
+  if (!s_last) return false;
+  // group level: half-warp h takes (k, c) = kb + (h & 1) for kb = 2 * warp, 2 * warp + CT / 16, ...
+  for (int kb = 2 * wrp; kb < NV * R; kb += CT / 16) {
+    const int kc = kb + ((threadIdx.x >> 4) & 1);
+    const bool on = kc < NV * R;
+    double v = on ? __ldcg(part + (size_t)kc * NCTA + grp * GSZ + (lane & 15)) : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) tot[kc / R][kc % R] = s;
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (on && (lane & 15) == 0) gpart[(size_t)kc * NGRP + grp] = v;
   }
   __syncthreads();
+  if (threadIdx.x == 0) {
+    st->gcnt[grp] = 0;
+    __threadfence();
+    s_last = atomicAdd(&st->cnt, 1u) == NGRP - 1;
+  }
+  __syncthreads();
+  if (!s_last) return false;
+  // last level: warp per (k, c), lanes over the group sums
+  for (int kc = wrp; kc < NV * R; kc += CT / 32) {
+    double v = lane < NGRP ? __ldcg(gpart + (size_t)kc * NGRP + lane) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) tot[kc / R][kc % R] = v;
+  }
+  __syncthreads();
+  return true;
 }
 
 // per-column CTA sums of NV values held one column per lane (lane % R) ->
@@ -173,7 +198,7 @@ __device__ __forceinline__ void column_partials(double (&v)[NV], double* part) {
     const int k = threadIdx.x / R, c = threadIdx.x % R;
     double s = 0;
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q][k][c];
-    part[((size_t)k * R + c) * gridDim.x + blockIdx.x] = s;
+    part[((size_t)k * R + c) * NCTA + blockIdx.x] = s;
     __threadfence();
   }
 }
@@ -200,62 +225,84 @@ __device__ __forceinline__ void load_nb6(const int32_t* __restrict__ nb6, int ro
 // stop flag (true residual within tolerance) and the correction target
 // eta = 0.5 tol |z| / |r| clamped to [ETA_MIN, 0.5].
 template <int R>
-__global__ void __launch_bounds__(CT) k_blk_outer(const BlkArgs* __restrict__ A, BlkState* st) {
+__global__ void __launch_bounds__(CT, 2) k_blk_outer(const BlkArgs* __restrict__ A, BlkState* st) {
   const int N = A->N;
   const float lam = A->lam;
   const int lane = threadIdx.x & 31, c = lane % R;
   constexpr int RPW = 32 / R;
   const int wrp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const float2* __restrict__ xm = A->xm;
+  const bool wsq = st->want_sq;
   int row0, row1;
   cta_rows(N, &row0, &row1);
   float fr = 0.0f, fz = 0.0f;
-  // warp-uniform trip count: the per-row sums over the columns below are shuffle trees
-  for (int base = row0 + wrp * RPW; base < row1; base += nw * RPW) {
-    const int row = base + lane / R;
-    const bool ok = row < row1;
-    float2 t = make_float2(0.f, 0.f);
-    if (ok) {
-      const size_t o = (size_t)row * R + c;
-      int nb[6];
-      load_nb6(A->nb6, row, nb);
-      float2 ns = make_float2(0.f, 0.f);
+  // warp-uniform trip count (the per-row sums over the columns below are shuffle trees); each step takes OU
+  // rows per lane group, with the neighbour tables and then all gathers of the OU rows issued before any is used
+  constexpr int OU = 2;
+  for (int base = row0 + wrp * RPW; base < row1; base += OU * nw * RPW) {
+    int rowu[OU], nb[OU][6];
+    bool oku[OU];
 #pragma unroll
-      for (int k = 0; k < 6; ++k)
-        if (nb[k] >= 0) ns = ff_add(ns, xm[(size_t)nb[k] * R + c]);
-      const float z = __bfloat162float(A->Z[o]);
-      const float2 xo = xm[o];
-      const float2 qx = ff_add(ff_mul_f(xo, __ldg(A->qd + row)), ff_neg(ff_mul_f(ns, lam)));
-      const float2 rf = ff_add_f(ff_neg(qx), z);
-      const float r = __fadd_rn(rf.x, rf.y);
-      A->r[st->par][o] = r;
-      fr += r * r;
-      fz += z * z;
-      t = make_float2(z * xo.x, z * xo.y);  // z = +-1 or 0: exact
+    for (int u = 0; u < OU; ++u) {
+      rowu[u] = base + u * nw * RPW + lane / R;
+      oku[u] = rowu[u] < row1;
+      if (oku[u]) {
+        load_nb6(A->nb6, rowu[u], nb[u]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) nb[u][k] = -1;
+      }
     }
-    // probe sums of this row (kept by the last residual pass of the block): float-float tree over the
-    // columns in a fixed order, then FP64
-    float2 qq = make_float2(0.f, 0.f);
-    if (A->hsq) {
-      const float p0 = __fmul_rn(t.x, t.x);
-      qq = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
+    float2 xn[OU][6], xo[OU];
+    float z[OU], q[OU];
+#pragma unroll
+    for (int u = 0; u < OU; ++u) {
+      const size_t o = (size_t)rowu[u] * R + c;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) xn[u][k] = nb[u][k] >= 0 ? xm[(size_t)nb[u][k] * R + c] : make_float2(0.f, 0.f);
+      xo[u] = oku[u] ? xm[o] : make_float2(0.f, 0.f);
+      z[u] = oku[u] ? __bfloat162float(A->Z[o]) : 0.0f;
+      q[u] = oku[u] ? __ldg(A->qd + rowu[u]) : 0.0f;
     }
 #pragma unroll
-    for (int o = R / 2; o > 0; o >>= 1) {
-      t = ff_add(t, make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o)));
-      if (A->hsq)
-        qq = ff_add(qq, make_float2(__shfl_xor_sync(0xffffffffu, qq.x, o), __shfl_xor_sync(0xffffffffu, qq.y, o)));
-    }
-    if (ok && c == 0) {
-      A->hsum[row] = (double)t.x + (double)t.y;
-      if (A->hsq) A->hsq[row] = (double)qq.x + (double)qq.y;
+    for (int u = 0; u < OU; ++u) {
+      float2 t = make_float2(0.f, 0.f);
+      if (oku[u]) {
+        float2 ns = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          if (nb[u][k] >= 0) ns = ff_add(ns, xn[u][k]);
+        const float2 qx = ff_add(ff_mul_f(xo[u], q[u]), ff_neg(ff_mul_f(ns, lam)));
+        const float2 rf = ff_add_f(ff_neg(qx), z[u]);
+        const float r = __fadd_rn(rf.x, rf.y);
+        A->r[st->par][(size_t)rowu[u] * R + c] = r;
+        fr += r * r;
+        fz += z[u] * z[u];
+        t = make_float2(z[u] * xo[u].x, z[u] * xo[u].y);  // z = +-1 or 0: exact
+      }
+      // probe sums of this row (kept by the last residual pass of the block): float-float tree over the
+      // columns in a fixed order, then FP64
+      float2 qq = make_float2(0.f, 0.f);
+      if (wsq) {
+        const float p0 = __fmul_rn(t.x, t.x);
+        qq = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
+      }
+#pragma unroll
+      for (int o = R / 2; o > 0; o >>= 1) {
+        t = ff_add(t, make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o)));
+        if (wsq)
+          qq = ff_add(qq, make_float2(__shfl_xor_sync(0xffffffffu, qq.x, o), __shfl_xor_sync(0xffffffffu, qq.y, o)));
+      }
+      if (oku[u] && c == 0) {
+        A->hsum[rowu[u]] = (double)t.x + (double)t.y;
+        if (wsq) A->hsq[rowu[u]] = (double)qq.x + (double)qq.y;
+      }
     }
   }
   double acc[2] = {(double)fr, (double)fz};
   column_partials<R, 2>(acc, A->part);
-  if (!arrive_last(&st->cnt)) return;
   __shared__ double tot[3][MAXR];
-  sum_partials<2>(A->part, R, gridDim.x, tot);
+  if (!reduce_partials<2>(A->part, A->gpart, st, R, tot)) return;
   if (threadIdx.x < R) {
     const int cc = threadIdx.x;
     const double rr = tot[0][cc], bb = tot[1][cc];
@@ -341,11 +388,10 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   constexpr int Q4 = R / 4;                          // float4 per row
   constexpr int OWN = SP_TR * Q4 / CT;               // own-row float4 per thread
   constexpr int XN = (SP_EMAX * Q4 + CT - 1) / CT;  // external float4 per thread (at most)
-  constexpr int RPW = 32 / R;
   static_assert(SP_TR * Q4 % CT == 0 && SP_TR == 16 * (CT / 32), "tile / CTA shape");
   const int N = A->N;
   const float lam = A->lam;
-  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5, c = lane % R;
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
   const int par = bench ? 0 : st->par;
   const float4* __restrict__ rA = reinterpret_cast<const float4*>(A->r[par]);
   const float4* __restrict__ wA = reinterpret_cast<const float4*>(A->w[par]);
@@ -487,7 +533,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       ft[0] += wn.x * uo.x; ft[1] += wn.y * uo.y; ft[2] += wn.z * uo.z; ft[3] += wn.w * uo.w;
     }
   }
-  // per-column CTA sums (lanes sharing threadIdx % Q4, then warps): r'.u', r'.r' -> part1, w'.u' -> part
+  // per-column CTA sums (lanes sharing threadIdx % Q4, then warps): r'.u', r'.r', w'.u' -> part1
   {
     __shared__ double sh1[CT / 32][8][12];
     double acc1[12];
@@ -507,22 +553,16 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       const int qk = threadIdx.x / R, cc = threadIdx.x % R;  // qk: 0 = r.u, 1 = r.r, 2 = w.u
       double t = 0.0;
       for (int ww = 0; ww < CT / 32; ++ww) t += sh1[ww][cc / 4][4 * qk + (cc & 3)];
-      if (qk < 2)
-        A->part1[((size_t)qk * R + cc) * gridDim.x + blockIdx.x] = t;
-      else
-        A->part[(size_t)cc * gridDim.x + blockIdx.x] = t;
+      A->part1[((size_t)qk * R + cc) * NCTA + blockIdx.x] = t;
     }
   }
-  if (!arrive_last(&st->cnt)) return;
+  __shared__ double tot1[3][MAXR];
+  if (!reduce_partials<3>(A->part1, A->gpart, st, R, tot1)) return;
   if (bench) {
     if (threadIdx.x == 0) st->cnt = 0;
     return;
   }
-  __shared__ double tot[3][MAXR];
-  __shared__ double tot1[3][MAXR];
   __shared__ int any_live;
-  sum_partials<1>(A->part, R, gridDim.x, tot);
-  sum_partials<2>(A->part1, R, gridDim.x, tot1);
   const bool first = st->first;
   if (threadIdx.x == 0) {
     any_live = 0;
@@ -531,7 +571,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
   __syncthreads();
   if (threadIdx.x < R) {
     const int cc = threadIdx.x;
-    const double gm = tot1[0][cc], rr = tot1[1][cc], d = tot[0][cc];
+    const double gm = tot1[0][cc], rr = tot1[1][cc], d = tot1[2][cc];
     if (!INIT) st->aprev[cc] = xhold ? (float)st->alpha[cc] : 0.0f;  // the alpha this iteration used
     if (!st->done[cc]) {
       if (first) {
@@ -746,7 +786,7 @@ __global__ void k_inv(int N, const float* __restrict__ qd, float* __restrict__ i
 // State for a new block of probes.  With xm = 0 the true residual is z
 // itself, so |r|^2 = |z|^2 = N for every live column and no residual pass is
 // needed before the first correction solve.
-__global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, int N, double eta_min) {
+__global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, int N, double eta_min, int want_sq) {
   int c = threadIdx.x;
   if (c < MAXR) {
     const int live = c < ncols;
@@ -765,9 +805,11 @@ __global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, in
     st->all_done = 0;
     st->status = 0;
     st->ncols = ncols;
+    st->want_sq = want_sq;
     st->first = 1;
     st->par = 0;  // k_probes wrote the first right-hand side into r[0]
     st->cnt = 0;
+    for (int q = 0; q < NGRP; ++q) st->gcnt[q] = 0;
     st->guard = 0;
     st->nexec = 0;
   }
@@ -781,6 +823,7 @@ __global__ void k_bench_state(BlkState* st) {
   }
   if (c == 0) {
     st->cnt = 0;
+    for (int q = 0; q < NGRP; ++q) st->gcnt[q] = 0;
     st->all_done = 0;
   }
 }
@@ -812,7 +855,7 @@ struct BlockGraph {
 
 static void free_arrays(BlockGraph* g) {
   void* ptrs[] = {g->h.r[0], g->h.w[0], g->h.s[0], g->h.r[1], g->h.w[1], g->h.s[1], g->h.p, g->h.x,
-                  g->h.xm, g->h.iq,       g->h.part, g->h.part1, g->Z, g->sacc, g->h.hsum, g->h.hsq};
+                  g->h.xm, g->h.iq,       g->h.part, g->h.part1, g->Z, g->sacc, g->h.hsum, g->h.hsq, g->h.gpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   g->cap_rows = 0;
@@ -906,7 +949,8 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     BF_CK(cudaMalloc(&g->h.iq, (size_t)rows * 4));
     BF_CK(cudaMalloc(&g->sacc, (size_t)rows * 8));
     BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NCTA * sizeof(double)));
-    BF_CK(cudaMalloc(&g->h.part1, (size_t)2 * R * NCTA * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.part1, (size_t)3 * R * NCTA * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.gpart, (size_t)3 * R * NGRP * sizeof(double)));
     g->cap_rows = rows;
   }
   if (!b->nb6) {
@@ -965,7 +1009,7 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
     int ncols = ke - k0 < R ? ke - k0 : R;
     k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.r[0]);
     count_launch();
-    k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols, N, ETA_MIN);
+    k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols, N, ETA_MIN, sq != nullptr);
     count_launch();
     blk_start<R>(g, s);
     BF_CK(cudaGetLastError());

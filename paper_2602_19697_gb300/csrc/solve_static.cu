@@ -100,8 +100,17 @@ __device__ bool reduce_all(double (&v)[NV], double* part, unsigned int* cnt, dou
   __syncthreads();
   if (!last) return false;
   for (int k = w; k < NV; k += SBT / 32) {
+    // the lane's partials in index order, eight loads in flight at a time
+    const double* p = part + (size_t)k * gridDim.x;
+    const int n = (int)gridDim.x;
     double s = 0;
-    for (int i = lane; i < (int)gridDim.x; i += 32) s += __ldcg(part + (size_t)k * gridDim.x + i);
+    for (int i0 = lane; i0 < n; i0 += 8 * 32) {
+      double v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) v[j] = i0 + 32 * j < n ? __ldcg(p + i0 + 32 * j) : 0.0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s += v[j];
+    }
     s = wsum(s);
     if (lane == 0) fin[k] = s;
   }

@@ -924,6 +924,9 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
     BF_CK(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
     BF_CK(cudaStreamBeginCaptureToGraph(g->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    // two iterations per evaluation of the WHILE condition (the launch gap between plain kernel nodes is
+    // shorter); the second one returns at once when the first finished the solve
+    blk_iter<R>(g, g->cap, h);
     blk_iter<R>(g, g->cap, h);
     cudaGraph_t ob;
     cudaError_t e = cudaStreamEndCapture(g->cap, &ob);

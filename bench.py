@@ -313,32 +313,36 @@ def run_ours(args, world, rank, local):
             "note": "single-RHS vectors of this workload are L2-resident (%.1f MB)" % (N * 12 / 1e6)}
     band.free()
 
-    # ---- end to end through the C ABI with pinned host buffers
+    # ---- end to end through the C ABI: pinned host frames in, host mu and s out
     e2e = None
     if not args.no_e2e:
         dh = torch.from_numpy(w.depth).pin_memory()
         ph = torch.from_numpy(w.poses).pin_memory()
+        muh = torch.empty(N, dtype=torch.float32).pin_memory()  # result buffers, allocated once
+        sh = torch.empty(N, dtype=torch.float32).pin_memory()
         e2e_t = []
         for i in range(2 + args.steps):
             stream.synchronize()
             t0 = time.perf_counter()
-            b = ctx.build_band_w(w, dh, ph)
-            b.integrate_depth(dh, ph, w.intr)
-            muh = torch.empty(b.N, dtype=torch.float32).pin_memory()
-            sh = torch.empty(b.N, dtype=torch.float32).pin_memory()
+            with torch.cuda.stream(stream):  # the step's inputs, copied once for the two calls that read them
+                dd = dh.to(dev, non_blocking=True)
+                pd = ph.to(dev, non_blocking=True)
+            b = ctx.build_band_w(w, dd, pd)
+            b.integrate_depth(dd, pd, w.intr)
+            if b.N != N:
+                raise RuntimeError("band size differs between runs")
             b.solve_mean(muh, rel_tol=args.tol)
             b.estimate_variance(sh, K=args.K, seed=0, rel_tol=args.tol, rhs_block=R)
             stream.synchronize()
             dt = time.perf_counter() - t0
             if i >= 2:
                 e2e_t.append(dt)
-            nb = b.N
             b.free()
         e2e_s = max_over_ranks(world, statistics.mean(e2e_t)) / world
-        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(2 * w.depth.nbytes + 2 * w.poses.nbytes),
-               "d2h_bytes_per_step": int(2 * nb * 4),
-               "note": "build_band + integrate_depth + solve_mean + estimate_variance from pinned host frames "
-                       "to host mu and s (frames staged by each of the two calls that read them)"}
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(w.depth.nbytes + w.poses.nbytes),
+               "d2h_bytes_per_step": int(2 * N * 4),
+               "note": "pinned host frames copied to the device once, then build_band + integrate_depth + "
+                       "solve_mean + estimate_variance through the C ABI, mu and s written to pinned host memory"}
 
     obj = None
     if world == 1 and not args.no_object:

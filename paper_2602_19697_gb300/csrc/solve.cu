@@ -325,15 +325,24 @@ __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, co
 }
 
 // True residual of the FP64 master iterate: r[0] = h - Q x64 (FP64), r.r and
-// h.h; the last CTA sets the stop flag and the correction target eta.
-template <class T>
+// h.h; the last CTA sets the stop flag and the correction target eta.  ZERO:
+// x64 is zero (a cold start), so r = h, read row by row without the SpMV.
+template <class T, bool ZERO = false>
 __global__ void __launch_bounds__(BT) k_outer(const SolveArgs<T>* __restrict__ A, PcgState* st) {
   __shared__ double tile[1000];
   __shared__ MetaWord sm[7][16];
   const BandView& B = A->B;
   const double* __restrict__ x64 = A->x64;
   double acc[2] = {0.0, 0.0};
-  for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
+  if (ZERO) {
+    for (int i = blockIdx.x * BT + threadIdx.x; i < B.N; i += gridDim.x * BT) {
+      const double h = (double)__ldg(A->rhs + i);
+      A->r[0][i] = (T)h;
+      acc[0] += h * h;
+      acc[1] += h * h;
+    }
+  }
+  for (int b = ZERO ? B.NB : blockIdx.x; b < B.NB; b += gridDim.x) {
     __syncthreads();
     load_meta(B, b, sm);
     __syncthreads();
@@ -718,7 +727,10 @@ static bf_status solve_t(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsi
   }
   k_state_init<<<1, 1, 0, s>>>(g->st, tol, max_iter, sizeof(T) == 8 ? 1e-14 : 1e-7);
   count_launch();
-  k_outer<T><<<NCTA, BT, 0, s>>>(A, g->st);
+  if (flags & BF_SOLVE_WARM)
+    k_outer<T><<<NCTA, BT, 0, s>>>(A, g->st);
+  else
+    k_outer<T, true><<<NCTA, BT, 0, s>>>(A, g->st);
   count_launch();
   k_cg_init<T><<<NCTA, BT, 0, s>>>(A, g->st);
   count_launch();

@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_outer(const BlkArgs* __restrict__
 // every CTA that stages it as an external neighbour):
 //   s' = w + beta s,  r' = r - alpha s',  u' = r' / Q_jj
 // (beta == 0 starts a new direction: the old s is not read).
+__device__ __forceinline__ void pf_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 __device__ __forceinline__ float bmul(float b, float v) { return b != 0.f ? __fmul_rn(b, v) : 0.f; }
 __device__ __forceinline__ float4 next_s(float4 w, float4 s, float4 be) {
   return make_float4(__fadd_rn(w.x, bmul(be.x, s.x)), __fadd_rn(w.y, bmul(be.y, s.y)), __fadd_rn(w.z, bmul(be.z, s.z)),
@@ -451,6 +452,10 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       const int q = threadIdx.x + i * CT;
       if (q >= nown) break;
       const size_t gq = (size_t)t0 * Q4 + q;
+      if (!INIT && q + CT < nown) {  // the thread's next item into L2
+        pf_l2(rA + gq + CT); pf_l2(wA + gq + CT); pf_l2(sA + gq + CT); pf_l2(p4 + gq + CT);
+        if (!xhold && xread) pf_l2(x4 + gq + CT);
+      }
       const float qi = __ldg(iq + t0 + q / Q4);
       const float4 ri = rA[gq];
       float4 rn, un;
@@ -497,6 +502,14 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       us4[SP_TR * Q4 + q] = un;
     }
     __syncthreads();
+    if (!INIT) {  // the thread's first item of the next tile into L2
+      const int tn = tile + gridDim.x;
+      if (tn < ntiles && (size_t)tn * SP_TR * Q4 + threadIdx.x < (size_t)N * Q4) {
+        const size_t gn = (size_t)tn * SP_TR * Q4 + threadIdx.x;
+        pf_l2(rA + gn); pf_l2(wA + gn); pf_l2(sA + gn); pf_l2(p4 + gn);
+        if (!xhold && xread) pf_l2(x4 + gn);
+      }
+    }
     // phase 3: w' = Q u' for the own rows, four columns (one float4 of u') per lane
     constexpr int RPS = 32 / Q4;  // rows per warp step
 #pragma unroll 1

@@ -300,9 +300,9 @@ def run_ours(args, world, rank, local):
     ms_spmv = band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=200)
     bytes_spmv = N * 12 + NB * (128 + 24)   # x, qd read, y written; brick metadata
     achieved = bytes_it / (ms_iter * 1e-3) / 1e9
-    # DRAM bytes (read + write) per launch from an ncu capture of this kernel on this band at R = 32; none yet for
-    # the current form of the kernel
-    traffic = None
+    # DRAM bytes (read + write) per launch from one ncu capture of this kernel on this band at R = 32
+    # (ncu --set full, 2 launches): mean of an x-writing launch (938.7 MB) and an x-holding one (727.7 MB)
+    traffic = 833234944 if (R_used == 32 and N == 640524) else None
     roof = {"kernel": "k_blk_it<%d> (one probe-solver iteration: vector updates and w = Q u in one pass, "
                       "the dominant kernel)" % R_used, "bound": "hbm",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),

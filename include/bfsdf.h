@@ -130,6 +130,19 @@ bf_status bf_export_band(bf_ctx* ctx, const bf_band* band, int64_t* lin, float* 
 bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* band, const float* depth, int T, const float* poses,
                              const bf_intrinsics* K);
 
+/* bf_integrate_depth with flags.  BF_INTEGRATE_DETERMINISTIC: the sums of w
+ * and w y are accumulated as int64 in units of 2^-32 (each FP32 sample
+ * rounded to the nearest unit, then added exactly), so they do not depend on
+ * the order in which concurrent updates land and repeated runs give the same
+ * bits; the FP32 sums of the default mode may differ in the last bits from
+ * run to run.  The totals are converted to FP32 after each call.  A band
+ * accumulates in one mode from its creation or its last
+ * bf_reset_observations: a call in the other mode returns BF_ESTATE.
+ * Totals must stay below 2^31 in magnitude.  Unknown flags: BF_EINVAL. */
+#define BF_INTEGRATE_DETERMINISTIC 1u
+bf_status bf_integrate_depth_ex(bf_ctx* ctx, bf_band* band, const float* depth, int T, const float* poses,
+                                const bf_intrinsics* K, unsigned flags);
+
 /* Reset the accumulated observations of a band to zero. */
 bf_status bf_reset_observations(bf_ctx* ctx, bf_band* band);
 

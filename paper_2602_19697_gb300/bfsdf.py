@@ -29,12 +29,14 @@ BF_SOLVE_FP64 = 1
 BF_SOLVE_WARM = 2
 
 EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_build_band", "bf_band_free",
-            "bf_band_info", "bf_export_band", "bf_integrate_depth", "bf_reset_observations", "bf_export_system",
+            "bf_band_info", "bf_export_band", "bf_integrate_depth", "bf_integrate_depth_ex", "bf_reset_observations",
+            "bf_export_system",
             "bf_spmv", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
             "bf_score_views", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
             "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
             "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance",
             "bf_net_bench", "bf_autotune_rhs_block"]
+BF_INTEGRATE_DETERMINISTIC = 1
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
 BF_NET_BENCH_FORWARD, BF_NET_BENCH_TRAIN, BF_NET_BENCH_CONV, BF_NET_BENCH_WGRAD, BF_NET_BENCH_CONV_MMA = range(5)
@@ -89,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "bf_band_info": (i, [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(i64)]),
         "bf_export_band": (i, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "bf_integrate_depth": (i, [vp, vp, vp, i, vp, ctypes.POINTER(Intrinsics)]),
+        "bf_integrate_depth_ex": (i, [vp, vp, vp, i, vp, ctypes.POINTER(Intrinsics), u]),
         "bf_reset_observations": (i, [vp, vp]),
         "bf_export_system": (i, [vp, vp, vp, vp, vp, vp]),
         "bf_spmv": (i, [vp, vp, vp, vp]),
@@ -246,7 +249,13 @@ class Band:
                                                    _ptr(out["mask"])), "bf_export_band")
         return out
 
-    def integrate_depth(self, depth, poses, K):
+    def integrate_depth(self, depth, poses, K, deterministic=False):
+        """Accumulate the frames' observations; deterministic=True sums them in int64 fixed point."""
+        if deterministic:
+            self.ctx.check(self.ctx.lib.bf_integrate_depth_ex(self.ctx._p, self._p, _ptr(depth), int(depth.shape[0]),
+                                                              _ptr(poses), ctypes.byref(_intr(K)),
+                                                              BF_INTEGRATE_DETERMINISTIC), "bf_integrate_depth_ex")
+            return
         self.ctx.check(self.ctx.lib.bf_integrate_depth(self.ctx._p, self._p, _ptr(depth), int(depth.shape[0]),
                                                        _ptr(poses), ctypes.byref(_intr(K))), "bf_integrate_depth")
 

@@ -182,7 +182,7 @@ void bf_band_free(bf_band* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   void* ptrs[] = {b->dir, b->bcoord, b->meta, b->off, b->nbr, b->lin, b->tsdf, b->wcount, b->info,
-                  b->d, b->hd, b->qd, b->rhs, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot};
+                  b->d, b->hd, b->qd, b->rhs, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot, b->dfx, b->hfx};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -238,19 +238,30 @@ bf_status bf_export_band(bf_ctx* ctx, const bf_band* b, int64_t* lin, float* tsd
   return BF_OK;
 }
 
-bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses,
-                             const bf_intrinsics* K) {
+bf_status bf_integrate_depth_ex(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses,
+                                const bf_intrinsics* K, unsigned flags) {
   if (!ctx || !b) return BF_EINVAL;
   if (!depth || !poses || T < 1 || !valid_intr(K))
     return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth: null pointer, T < 1 or bad intrinsics");
+  if (flags & ~BF_INTEGRATE_DETERMINISTIC) return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth_ex: unknown flags");
   const float *d_depth, *d_poses;
   BF_TRY(stage_in(ctx, depth, (size_t)T * K->H * K->W, WS_STAGE0, &d_depth));
   BF_TRY(stage_in(ctx, poses, (size_t)T * 12, WS_STAGE1, &d_poses));
-  return band_integrate(ctx, b, d_depth, T, d_poses, to_intr(K));
+  return band_integrate(ctx, b, d_depth, T, d_poses, to_intr(K), (flags & BF_INTEGRATE_DETERMINISTIC) != 0);
+}
+
+bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses,
+                             const bf_intrinsics* K) {
+  return bf_integrate_depth_ex(ctx, b, depth, T, poses, K, 0u);
 }
 
 bf_status bf_reset_observations(bf_ctx* ctx, bf_band* b) {
   if (!ctx || !b) return BF_EINVAL;
+  b->obs_mode = 0;
+  if (b->dfx) {
+    BF_CK(cudaMemsetAsync(b->dfx, 0, (b->N ? b->N : 1) * sizeof(int64_t), ctx->stream));
+    BF_CK(cudaMemsetAsync(b->hfx, 0, (b->N ? b->N : 1) * sizeof(int64_t), ctx->stream));
+  }
   if (b->d) {
     BF_CK(cudaMemsetAsync(b->d, 0, b->N * 4, ctx->stream));
     BF_CK(cudaMemsetAsync(b->hd, 0, b->N * 4, ctx->stream));

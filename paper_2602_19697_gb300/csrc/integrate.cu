@@ -5,17 +5,23 @@
 // k_integrate: one thread per pixel (consecutive threads = consecutive pixels
 // of a row, so depth loads coalesce).  The pixel ray's segment [s_p - tau,
 // s_p + tau] is walked by the FP32-spec DDA; each band voxel entered gets
-// d += w, hdata += w y through L2 atomics (fire-and-forget reductions).
+// d += w, hdata += w y through L2 atomics (fire-and-forget reductions).  The
+// FP32 sums depend on the order the atomics land in; with FIX the FP32
+// samples w and w y are added instead as int64 in units of 2^-32 (rounded to
+// the nearest unit, exact from there on, so the sums do not depend on the
+// order) and k_fix_out converts the totals to FP32.
 // k_assemble: Q_jj = lambda deg + lambda_b [dB] + d, h = hdata + lambda_b
 // [dB] tsdf / h.
 #include "internal.cuh"
 
 namespace {
 
+template <bool FIX>
 __global__ void __launch_bounds__(256) k_integrate(BandView B, const float* __restrict__ depth, int T, Intr K,
                                                    const float* __restrict__ poses, float tau, int max_steps,
                                                    float sa, float sb, float s2_extra, float* __restrict__ d,
-                                                   float* __restrict__ hd) {
+                                                   float* __restrict__ hd, int64_t* __restrict__ dfx,
+                                                   int64_t* __restrict__ hfx) {
   int64_t npix = (int64_t)T * K.H * K.W;
   const float org[3] = {B.o0, B.o1, B.o2};
   const float h = B.h, inv_h = 1.0f / B.h;
@@ -38,9 +44,25 @@ __global__ void __launch_bounds__(256) k_integrate(BandView B, const float* __re
       float x0 = B.o0 + ((float)i + 0.5f) * h, x1 = B.o1 + ((float)j + 0.5f) * h, x2 = B.o2 + ((float)k + 0.5f) * h;
       float y = ray.r[0] * (p0 - x0) + ray.r[1] * (p1 - x1) + ray.r[2] * (p2 - x2);
       y = fminf(fmaxf(y, -tau), tau) * inv_h;
-      atomicAdd(d + v, w);
-      atomicAdd(hd + v, w * y);
+      if (FIX) {
+        const float scale = (float)(1ull << OBS_FIX_BITS);
+        atomicAdd(reinterpret_cast<unsigned long long*>(dfx + v), (unsigned long long)__float2ll_rn(w * scale));
+        atomicAdd(reinterpret_cast<unsigned long long*>(hfx + v), (unsigned long long)__float2ll_rn((w * y) * scale));
+      } else {
+        atomicAdd(d + v, w);
+        atomicAdd(hd + v, w * y);
+      }
     });
+  }
+}
+
+// d, hd = the fixed-point totals in FP32
+__global__ void k_fix_out(int N, const int64_t* __restrict__ dfx, const int64_t* __restrict__ hfx, float* __restrict__ d,
+                          float* __restrict__ hd) {
+  const double unit = 1.0 / (double)(1ull << OBS_FIX_BITS);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+    d[v] = (float)((double)dfx[v] * unit);
+    hd[v] = (float)((double)hfx[v] * unit);
   }
 }
 
@@ -63,9 +85,20 @@ unsigned grid_for(int64_t n, int threads) {
 
 }  // namespace
 
-bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses, const Intr& K) {
+bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses, const Intr& K,
+                         bool fixed_point) {
   cudaStream_t s = ctx->stream;
   bf_status st;
+  const int mode = fixed_point ? 2 : 1;
+  if (b->obs_mode != 0 && b->obs_mode != mode)
+    return bf_fail(ctx, BF_ESTATE, "bf_integrate_depth: the band accumulates in the other mode since its last "
+                                   "bf_reset_observations");
+  if (fixed_point && !b->dfx) {
+    if ((st = dev_alloc_t(ctx, &b->dfx, b->N ? b->N : 1))) return st;
+    if ((st = dev_alloc_t(ctx, &b->hfx, b->N ? b->N : 1))) return st;
+    BF_CK(cudaMemsetAsync(b->dfx, 0, (b->N ? b->N : 1) * sizeof(int64_t), s));
+    BF_CK(cudaMemsetAsync(b->hfx, 0, (b->N ? b->N : 1) * sizeof(int64_t), s));
+  }
   if (!b->d) {
     if ((st = dev_alloc_t(ctx, &b->d, b->N ? b->N : 1))) return st;
     if ((st = dev_alloc_t(ctx, &b->hd, b->N ? b->N : 1))) return st;
@@ -79,9 +112,21 @@ bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, con
     float tau = (float)p.band_vox * b->grid.voxel;
     float s2x = (float)(p.sig_pose * p.sig_pose + p.sig_model * p.sig_model);
     int64_t npix = (int64_t)T * K.H * K.W;
-    k_integrate<<<grid_for(npix, 256), 256, 0, s>>>(band_view(b), depth, T, K, poses, tau, dda_max_steps(p.band_vox),
-                                                   (float)p.sig_a, (float)p.sig_b, s2x, b->d, b->hd); count_launch();
+    if (fixed_point) {
+      k_integrate<true><<<grid_for(npix, 256), 256, 0, s>>>(band_view(b), depth, T, K, poses, tau,
+                                                            dda_max_steps(p.band_vox), (float)p.sig_a, (float)p.sig_b,
+                                                            s2x, b->d, b->hd, b->dfx, b->hfx);
+      count_launch();
+      k_fix_out<<<grid_for(b->N, 256), 256, 0, s>>>((int)b->N, b->dfx, b->hfx, b->d, b->hd);
+      count_launch();
+    } else {
+      k_integrate<false><<<grid_for(npix, 256), 256, 0, s>>>(band_view(b), depth, T, K, poses, tau,
+                                                             dda_max_steps(p.band_vox), (float)p.sig_a,
+                                                             (float)p.sig_b, s2x, b->d, b->hd, nullptr, nullptr);
+      count_launch();
+    }
     BF_CK(cudaGetLastError());
+    b->obs_mode = mode;
   }
   return band_assemble(ctx, b);
 }

@@ -87,6 +87,10 @@ struct bf_band {
   uint8_t* info = nullptr;    // [N] deg | bdry << 3
   float* d = nullptr;         // [N] sum w
   float* hd = nullptr;        // [N] sum w y
+  // deterministic accumulation: sum w and sum w y as int64 in units of 2^-OBS_FIX_BITS (exact, order-free)
+  int64_t* dfx = nullptr;
+  int64_t* hfx = nullptr;
+  int obs_mode = 0;           // observations accumulated since the last reset: 0 none, 1 FP32 atomics, 2 fixed point
   float* qd = nullptr;        // [N] Q_jj
   float* rhs = nullptr;       // [N] h_j
   bool integrated = false;
@@ -169,7 +173,9 @@ bf_status scan_i32(bf_ctx* ctx, const int32_t* in, int32_t* out, int64_t n, int3
 // Module entry points (host side of each .cu file).
 bf_status band_build(bf_ctx* ctx, const float* depth, int T, const float* poses, const Intr& K, const bf_grid& g,
                      const bf_params& p, bf_band** out);
-bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses, const Intr& K);
+bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses, const Intr& K,
+                         bool fixed_point = false);
+constexpr int OBS_FIX_BITS = 32;
 bf_status band_assemble(bf_ctx* ctx, bf_band* b);
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
 bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,

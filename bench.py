@@ -52,7 +52,8 @@ def parse():
                     help="skip the 512^3 object-sequence measurements (SpMV vs HBM peak, batched vs unbatched)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget (s)")
     ap.add_argument("--kernel", default=None,
-                    choices=["block_iter", "spmv", "net_forward", "net_train", "net_conv", "net_conv_mma", "net_wgrad"],
+                    choices=["block_iter", "spmv", "spmm", "net_forward", "net_train", "net_conv", "net_conv_mma",
+                             "net_wgrad"],
                     help="time one kernel alone on the workload's band (for profiling): --warmup untimed and "
                          "--steps timed launches; prints one JSON line with its throughput")
     return ap.parse_args()
@@ -480,9 +481,9 @@ def run_kernel(args):
         ms = band.bench_kernel(which, R=R, reps=max(args.steps, 1))
         nbytes = N * (R * 36 + 8)
         out.update(ms_per_launch=ms, bytes_per_launch=nbytes, achieved_gbs=nbytes / (ms * 1e-3) / 1e9)
-    elif args.kernel == "spmv":
-        which = bfsdf.BF_KERNEL_SPMV
-        band.bench_kernel(which, reps=max(args.warmup, 1))
+    elif args.kernel in ("spmv", "spmm"):
+        which = bfsdf.BF_KERNEL_SPMV if args.kernel == "spmv" else bfsdf.BF_KERNEL_SPMM
+        band.bench_kernel(which, R=R, reps=max(args.warmup, 1))
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device="cuda")
         clean = torch.zeros(256 * 1024 * 1024, dtype=torch.float32, device="cuda")
         ms = []
@@ -490,13 +491,15 @@ def run_kernel(args):
             flush.fill_(float(i))
             clean.sum()
             torch.cuda.synchronize()
-            ms.append(band.bench_kernel(which, reps=1))
-        nbytes = N * 12 + NB * (128 + 24)
+            ms.append(band.bench_kernel(which, R=R, reps=1))
+        # x (or X) and Q_jj read, y (or Y) written, brick metadata
+        nbytes = N * 12 + NB * (128 + 24) if args.kernel == "spmv" else N * (8 * R + 4) + NB * (128 + 24)
         med = float(np.median(ms))
         hbm, peak_kind = peaks()
         out.update(ms_per_launch=med, ms_min=min(ms), bytes_per_launch=nbytes,
                    achieved_gbs=nbytes / (med * 1e-3) / 1e9, peak_gbs=hbm, peak_kind=peak_kind,
                    frac=nbytes / (med * 1e-3) / 1e9 / hbm, bytes_per_voxel=nbytes / N,
+                   columns=(R if args.kernel == "spmm" else 1),
                    l2="1 GB written, then another 1 GB read, before each single launch; median")
     else:
         net = bfsdf.Net(ctx, seed=0)

@@ -140,6 +140,12 @@ bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* band, const float* depth, int
  * bf_reset_observations: a call in the other mode returns BF_ESTATE.
  * Totals must stay below 2^31 in magnitude.  Unknown flags: BF_EINVAL. */
 #define BF_INTEGRATE_DETERMINISTIC 1u
+
+/* The observation sums d = sum w and hdata = sum w y in FP64 ([N] double
+ * each, device or host; NULL skips): after deterministic integration the
+ * int64 fixed-point totals converted exactly (to 53 bits), else the FP32
+ * sums widened.  BF_ESTATE before bf_integrate_depth. */
+bf_status bf_export_observations_f64(bf_ctx* ctx, const bf_band* band, double* d, double* hdata);
 bf_status bf_integrate_depth_ex(bf_ctx* ctx, bf_band* band, const float* depth, int T, const float* poses,
                                 const bf_intrinsics* K, unsigned flags);
 
@@ -153,6 +159,13 @@ bf_status bf_export_system(bf_ctx* ctx, const bf_band* band, float* d, float* hd
 /* y = Q x for x, y [N] float (Sec. 3.6 precision equation; matrix-free
  * 7-point stencil: (Qx)_j = Q_jj x_j - lambda sum_{6-nbrs k in B} x_k). */
 bf_status bf_spmv(bf_ctx* ctx, const bf_band* band, const float* x, float* y);
+
+/* Y = Q X for R right-hand sides at once (Sec. 3.6 precision equation, the
+ * same stencil and summation order as bf_spmv).  X, Y [N][R] float, the R
+ * values of a voxel contiguous (device or host; host memory is staged).
+ * R = 8, 16 or 32, else BF_EINVAL; BF_ESTATE before bf_integrate_depth.
+ * The first call on a band builds its SpMM gather plan (kept with the band). */
+bf_status bf_spmm(bf_ctx* ctx, bf_band* band, const float* X, int R, float* Y);
 
 /* MAP mean: solve Q mu = h by Jacobi-preconditioned CG (Sec. 3.6, MAP
  * equation; Algorithm 1 step 5).  Stops when ||r||_2 <= rel_tol ||h||_2 on
@@ -332,10 +345,12 @@ bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* band, int which,
  * and returns the mean time per repetition (ms).
  *   BF_KERNEL_SPMV: the 7-point SpMV y = Q x over the band (bf_spmv's kernel);
  *   BF_KERNEL_BLOCK_ITER: one probe-solver iteration over R = 8, 16 or 32
- *     columns (the single-pass kernel: vector updates and w = Q u).
+ *     columns (the single-pass kernel: vector updates and w = Q u);
+ *   BF_KERNEL_SPMM: Y = Q X over R = 8, 16 or 32 columns (bf_spmm's kernel).
  * Inputs are the library's own workspaces (their values are not preserved). */
 #define BF_KERNEL_SPMV 0
 #define BF_KERNEL_BLOCK_ITER 1
+#define BF_KERNEL_SPMM 2
 bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* band, int which, int R, int reps, double* ms_per_launch);
 
 /* Number of GPU kernels this library has run in this process (host launches

@@ -29,9 +29,10 @@ BF_SOLVE_FP64 = 1
 BF_SOLVE_WARM = 2
 
 EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_build_band", "bf_band_free",
-            "bf_band_info", "bf_export_band", "bf_integrate_depth", "bf_integrate_depth_ex", "bf_reset_observations",
+            "bf_band_info", "bf_export_band", "bf_integrate_depth", "bf_integrate_depth_ex", "bf_export_observations_f64",
+            "bf_reset_observations",
             "bf_export_system",
-            "bf_spmv", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
+            "bf_spmv", "bf_spmm", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
             "bf_score_views", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
             "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
             "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance",
@@ -39,6 +40,7 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
 BF_INTEGRATE_DETERMINISTIC = 1
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
+BF_KERNEL_SPMM = 2
 BF_NET_BENCH_FORWARD, BF_NET_BENCH_TRAIN, BF_NET_BENCH_CONV, BF_NET_BENCH_WGRAD, BF_NET_BENCH_CONV_MMA = range(5)
 # algorithmic FLOPs of the network per brick tile (10^3 voxels, 27 taps, real channels)
 NET_FLOPS_FWD = 2 * 1000 * 27 * (2 * 32 + 32 * 32 + 32 * 32 + 32 * 2)
@@ -92,9 +94,11 @@ def load_library(path: str = LIB_PATH):
         "bf_export_band": (i, [vp, vp, vp, vp, vp, vp, vp, vp]),
         "bf_integrate_depth": (i, [vp, vp, vp, i, vp, ctypes.POINTER(Intrinsics)]),
         "bf_integrate_depth_ex": (i, [vp, vp, vp, i, vp, ctypes.POINTER(Intrinsics), u]),
+        "bf_export_observations_f64": (i, [vp, vp, vp, vp]),
         "bf_reset_observations": (i, [vp, vp]),
         "bf_export_system": (i, [vp, vp, vp, vp, vp, vp]),
         "bf_spmv": (i, [vp, vp, vp, vp]),
+        "bf_spmm": (i, [vp, vp, vp, i, vp]),
         "bf_solve_mean": (i, [vp, vp, d, i, u, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "bf_estimate_variance": (i, [vp, vp, i, ctypes.c_uint64, d, i, i, u, vp, ctypes.POINTER(i)]),
         "bf_extract_surface": (i, [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
@@ -259,6 +263,13 @@ class Band:
         self.ctx.check(self.ctx.lib.bf_integrate_depth(self.ctx._p, self._p, _ptr(depth), int(depth.shape[0]),
                                                        _ptr(poses), ctypes.byref(_intr(K))), "bf_integrate_depth")
 
+    def export_observations_f64(self):
+        """(d, hdata) as FP64 numpy arrays."""
+        d, hd = np.empty(self.N, np.float64), np.empty(self.N, np.float64)
+        self.ctx.check(self.ctx.lib.bf_export_observations_f64(self.ctx._p, self._p, _ptr(d), _ptr(hd)),
+                       "bf_export_observations_f64")
+        return d, hd
+
     def reset_observations(self):
         self.ctx.check(self.ctx.lib.bf_reset_observations(self.ctx._p, self._p), "bf_reset_observations")
 
@@ -272,6 +283,13 @@ class Band:
     def spmv(self, x, y):
         self.ctx.check(self.ctx.lib.bf_spmv(self.ctx._p, self._p, _ptr(x), _ptr(y)), "bf_spmv")
         return y
+
+    def spmm(self, X, Y):
+        """Y = Q X for X, Y of shape [N, R] (R = 8, 16 or 32, rows contiguous)."""
+        if X.shape != Y.shape or X.shape[0] != self.N:
+            raise ValueError("X and Y must both have shape [N, R]")
+        self.ctx.check(self.ctx.lib.bf_spmm(self.ctx._p, self._p, _ptr(X), int(X.shape[1]), _ptr(Y)), "bf_spmm")
+        return Y
 
     def solve_mean(self, mu, rel_tol=1e-6, max_iter=20000, fp64=False, warm=False, raise_on_fail=True):
         it, rr = ctypes.c_int(), ctypes.c_double()

@@ -286,6 +286,20 @@ bf_status bf_export_system(bf_ctx* ctx, const bf_band* b, float* d, float* hdata
   return BF_OK;
 }
 
+bf_status bf_export_observations_f64(bf_ctx* ctx, const bf_band* b, double* d, double* hdata) {
+  if (!ctx || !b) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_export_observations_f64: call bf_integrate_depth first");
+  if (!b->N || (!d && !hdata)) return BF_OK;
+  double *dd = nullptr, *dh = nullptr;
+  bool host_d = false, host_h = false;
+  if (d) BF_TRY(stage_out(ctx, d, b->N, WS_OUT0, &dd, &host_d));
+  if (hdata) BF_TRY(stage_out(ctx, hdata, b->N, WS_OUT1, &dh, &host_h));
+  BF_TRY(band_observations_f64(ctx, b, dd, dh));
+  if (d) BF_TRY(copy_out(ctx, d, (const double*)dd, b->N, host_d));
+  if (hdata) BF_TRY(copy_out(ctx, hdata, (const double*)dh, b->N, host_h));
+  return BF_OK;
+}
+
 bf_status bf_spmv(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   if (!ctx || !b || !x || !y) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_spmv: call bf_integrate_depth first");
@@ -296,6 +310,20 @@ bf_status bf_spmv(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   BF_TRY(stage_out(ctx, y, b->N, WS_OUT0, &dy, &host));
   BF_TRY(spmv_launch(ctx, b, dx, dy));
   return copy_out(ctx, y, (const float*)dy, b->N, host);
+}
+
+bf_status bf_spmm(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y) {
+  if (!ctx || !b || !X || !Y) return BF_EINVAL;
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_spmm: call bf_integrate_depth first");
+  if (R != 8 && R != 16 && R != 32) return bf_fail(ctx, BF_EINVAL, "bf_spmm: R must be 8, 16 or 32");
+  const float* dX;
+  float* dY;
+  bool host;
+  const size_t n = (size_t)b->N * R;
+  BF_TRY(stage_in(ctx, X, n, WS_STAGE2, &dX));
+  BF_TRY(stage_out(ctx, Y, n, WS_OUT0, &dY, &host));
+  BF_TRY(spmm_launch(ctx, b, dX, R, dY));
+  return copy_out(ctx, Y, (const float*)dY, n, host);
 }
 
 bf_status bf_solve_mean(bf_ctx* ctx, bf_band* b, double rel_tol, int max_iter, unsigned flags, float* mu,
@@ -393,18 +421,27 @@ bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, d
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_bench_kernel: call bf_integrate_depth first");
   if (b->N == 0) return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: empty band");
   cudaStream_t s = ctx->stream;
-  if (which == BF_KERNEL_SPMV) {
+  if (which == BF_KERNEL_SPMV || which == BF_KERNEL_SPMM) {
+    if (which == BF_KERNEL_SPMM && R != 8 && R != 16 && R != 32)
+      return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: R must be 8, 16 or 32");
+    const int cols = which == BF_KERNEL_SPMM ? R : 1;
+    const size_t bytes = (size_t)b->N * cols * 4;
     bf_status st;
-    float* x = (float*)ws_get(ctx, WS_TMP0, (size_t)b->N * 4, &st);
+    float* x = (float*)ws_get(ctx, WS_TMP0, bytes, &st);
     if (st) return st;
-    float* y = (float*)ws_get(ctx, WS_TMP1, (size_t)b->N * 4, &st);
+    float* y = (float*)ws_get(ctx, WS_TMP1, bytes, &st);
     if (st) return st;
-    BF_CK(cudaMemsetAsync(x, 0, (size_t)b->N * 4, s));
+    BF_CK(cudaMemsetAsync(x, 0, bytes, s));
+    if (which == BF_KERNEL_SPMM) BF_TRY(spmm_launch(ctx, b, x, R, y));  // builds the gather plan outside the timing
     cudaEvent_t e0, e1;
     BF_CK(cudaEventCreate(&e0));
     BF_CK(cudaEventCreate(&e1));
     BF_CK(cudaEventRecord(e0, s));
-    for (int i = 0; i < reps; ++i) BF_TRY(spmv_launch(ctx, b, (i & 1) ? y : x, (i & 1) ? x : y));
+    for (int i = 0; i < reps; ++i) {
+      float* in = (i & 1) ? y : x;
+      float* out = (i & 1) ? x : y;
+      BF_TRY(which == BF_KERNEL_SPMM ? spmm_launch(ctx, b, in, R, out) : spmv_launch(ctx, b, in, out));
+    }
     BF_CK(cudaEventRecord(e1, s));
     BF_CK(cudaEventSynchronize(e1));
     float t = 0;

@@ -664,6 +664,87 @@ __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed,
   }
 }
 
+// Y = Q X for R right-hand sides (X, Y [N][R], the columns of a row
+// contiguous): the matrix-free 7-point stencil of the precision (Sec. 3.6),
+// applied per tile of SP_TR rows with the tile's own rows and its external
+// face-neighbour rows (the band's gather plan) staged in shared memory, then
+// four columns of a row per lane; the neighbour sum keeps the order
+// ((x-1 + x+1) + (y-1 + y+1)) + (z-1 + z+1) of the single-RHS SpMV.
+template <int R>
+__global__ void __launch_bounds__(CT, 2) k_spmm(int N, float lam, const float* __restrict__ qd,
+                                                const int32_t* __restrict__ nb6, const int32_t* __restrict__ sp_ext,
+                                                const int32_t* __restrict__ sp_ne, const int16_t* __restrict__ sp_slot,
+                                                const float* __restrict__ X, float* __restrict__ Y) {
+  constexpr int Q4 = R / 4;
+  constexpr int OWN = SP_TR * Q4 / CT;
+  constexpr int XN = (SP_EMAX * Q4 + CT - 1) / CT;
+  static_assert(SP_TR * Q4 % CT == 0 && SP_TR == 16 * (CT / 32), "tile / CTA shape");
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5, g = threadIdx.x % Q4;
+  const float4* __restrict__ X4 = reinterpret_cast<const float4*>(X);
+  float4* __restrict__ Y4 = reinterpret_cast<float4*>(Y);
+  extern __shared__ __align__(16) float us[];  // [SP_ROWS][R]
+  float4* us4 = reinterpret_cast<float4*>(us);
+  const int ntiles = (N + SP_TR - 1) / SP_TR;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int t0 = tile * SP_TR, t1 = min(N, t0 + SP_TR);
+    const int ne = __ldg(sp_ne + tile);
+    const int32_t* __restrict__ ext = sp_ext + (size_t)tile * SP_EMAX;
+    uint4 slv = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    float qv = 0.0f;
+    {
+      const int myrow = t0 + 16 * wrp + (lane & 15);
+      if (lane < 16 && myrow < t1) {
+        slv = __ldg(reinterpret_cast<const uint4*>(sp_slot) + myrow);
+        qv = __ldg(qd + myrow);
+      }
+    }
+    int ji[XN];
+#pragma unroll
+    for (int i = 0; i < XN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      ji[i] = q < SP_EMAX * Q4 ? __ldg(ext + q / Q4) : 0;
+    }
+    __syncthreads();  // the previous tile's readers of us are done
+    const int nown = (t1 - t0) * Q4;
+#pragma unroll
+    for (int i = 0; i < OWN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      if (q < nown) us4[q] = __ldg(X4 + (size_t)t0 * Q4 + q);
+    }
+    const int next = ne * Q4;
+#pragma unroll
+    for (int i = 0; i < XN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      if (q < next) us4[SP_TR * Q4 + q] = __ldg(X4 + (size_t)ji[i] * Q4 + (q % Q4));
+    }
+    __syncthreads();
+    constexpr int RPS = 32 / Q4;  // rows per warp step
+#pragma unroll 1
+    for (int jstep = 0; jstep < 16 / RPS; ++jstep) {
+      const int src = jstep * RPS + lane / Q4;  // row of the warp's 16, and the lane holding its slots
+      const int rr = 16 * wrp + src, row = t0 + rr;
+      const uint32_t sx = __shfl_sync(0xffffffffu, slv.x, src), sy = __shfl_sync(0xffffffffu, slv.y, src),
+                     sz = __shfl_sync(0xffffffffu, slv.z, src);
+      const float q = __shfl_sync(0xffffffffu, qv, src);
+      if (row >= t1) continue;
+      const int sv[6] = {(int16_t)(sx & 0xffffu), (int16_t)(sx >> 16), (int16_t)(sy & 0xffffu),
+                         (int16_t)(sy >> 16),     (int16_t)(sz & 0xffffu), (int16_t)(sz >> 16)};
+      const float4 xo = us4[rr * Q4 + g];
+      auto nbx = [&](int k) -> float4 {  // staged row, or read from global memory beyond the staged list
+        const int sk = sv[k];
+        if (sk >= 0 && sk != SP_GLOBAL) return us4[sk * Q4 + g];
+        if (sk < 0) return make_float4(0.f, 0.f, 0.f, 0.f);
+        return __ldg(X4 + (size_t)__ldg(nb6 + 6 * (size_t)row + k) * Q4 + g);
+      };
+      auto add4 = [](float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); };
+      const float4 s01 = add4(nbx(0), nbx(1)), s23 = add4(nbx(2), nbx(3)), s45 = add4(nbx(4), nbx(5));
+      const float4 ns = add4(add4(s01, s23), s45);
+      Y4[(size_t)row * Q4 + g] = make_float4(q * xo.x - lam * ns.x, q * xo.y - lam * ns.y, q * xo.z - lam * ns.z,
+                                             q * xo.w - lam * ns.w);
+    }
+  }
+}
+
 __global__ void k_finish(int N, const double* __restrict__ sacc, double invK, float* __restrict__ s) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) s[i] = (float)(sacc[i] * invK);
 }
@@ -908,6 +989,28 @@ static void blk_outer(BlockGraph* g, cudaStream_t s) {
 
 static int ridx(int R) { return R == 8 ? 0 : (R == 16 ? 1 : 2); }
 
+// The band's face-neighbour table and SpMM gather plan (built once per band).
+static bf_status ensure_sp_plan(bf_ctx* ctx, bf_band* b) {
+  cudaStream_t s = ctx->stream;
+  if (!b->nb6) {
+    BF_TRY(dev_alloc_t(ctx, &b->nb6, (size_t)6 * (b->N ? b->N : 1)));
+    k_nb6<<<grid_for(b->N, 256, 152 * 16), 256, 0, s>>>(band_view(b), b->nb6);
+    count_launch();
+  }
+  if (!b->sp_slot) {
+    const int nt = (int)((b->N + SP_TR - 1) / SP_TR);
+    BF_TRY(dev_alloc_t(ctx, &b->sp_ext, (size_t)SP_EMAX * (nt ? nt : 1)));
+    BF_TRY(dev_alloc_t(ctx, &b->sp_ne, (size_t)(nt ? nt : 1)));
+    BF_TRY(dev_alloc_t(ctx, &b->sp_slot, (size_t)8 * (b->N ? b->N : 1)));
+    if (nt) {
+      k_sp_plan<<<nt, 256, 0, s>>>((int)b->N, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot);
+      count_launch();
+    }
+  }
+  BF_CK(cudaGetLastError());
+  return BF_OK;
+}
+
 // The context's block solver for width R, with workspaces for >= N rows and
 // the argument block pointing at band b.
 template <int R>
@@ -969,21 +1072,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     BF_CK(cudaMalloc(&g->h.gpart, (size_t)3 * R * NGRP * sizeof(double)));
     g->cap_rows = rows;
   }
-  if (!b->nb6) {
-    BF_TRY(dev_alloc_t(ctx, &b->nb6, (size_t)6 * (b->N ? b->N : 1)));
-    k_nb6<<<grid_for(b->N, 256, 152 * 16), 256, 0, s>>>(band_view(b), b->nb6);
-    count_launch();
-  }
-  if (!b->sp_slot) {
-    const int nt = (int)((b->N + SP_TR - 1) / SP_TR);
-    BF_TRY(dev_alloc_t(ctx, &b->sp_ext, (size_t)SP_EMAX * (nt ? nt : 1)));
-    BF_TRY(dev_alloc_t(ctx, &b->sp_ne, (size_t)(nt ? nt : 1)));
-    BF_TRY(dev_alloc_t(ctx, &b->sp_slot, (size_t)8 * (b->N ? b->N : 1)));
-    if (nt) {
-      k_sp_plan<<<nt, 256, 0, s>>>((int)b->N, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot);
-      count_launch();
-    }
-  }
+  BF_TRY(ensure_sp_plan(ctx, b));
   g->h.N = (int)b->N;
   g->h.lam = (float)b->prm.lambda;
   g->h.nb6 = b->nb6;
@@ -1189,4 +1278,25 @@ bf_status variance_impl(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, u
     case 32: return variance_t<32>(ctx, b, kb, ke, scale, seed, tol, max_iter, s, total_iters, sq, s1);
   }
   return bf_fail(ctx, BF_EINVAL, "rhs_block must be 0, 1, 8, 16 or 32");
+}
+
+template <int R>
+static bf_status spmm_t(bf_ctx* ctx, bf_band* b, const float* X, float* Y) {
+  BF_CK(cudaFuncSetAttribute(k_spmm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
+  BF_TRY(ensure_sp_plan(ctx, b));
+  k_spmm<R><<<NCTA, CT, sp_smem(R), ctx->stream>>>((int)b->N, (float)b->prm.lambda, b->qd, b->nb6, b->sp_ext,
+                                                   b->sp_ne, b->sp_slot, X, Y);
+  count_launch();
+  BF_CK(cudaGetLastError());
+  return BF_OK;
+}
+
+bf_status spmm_launch(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y) {
+  if (b->N == 0) return BF_OK;
+  switch (R) {
+    case 8: return spmm_t<8>(ctx, b, X, Y);
+    case 16: return spmm_t<16>(ctx, b, X, Y);
+    case 32: return spmm_t<32>(ctx, b, X, Y);
+    default: return bf_fail(ctx, BF_EINVAL, "bf_spmm: R must be 8, 16 or 32");
+  }
 }

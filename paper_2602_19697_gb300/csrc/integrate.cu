@@ -66,6 +66,17 @@ __global__ void k_fix_out(int N, const int64_t* __restrict__ dfx, const int64_t*
   }
 }
 
+// FP64 copies of the observation sums: the fixed-point totals exactly (to 53 bits), else the FP32 sums
+__global__ void k_obs_f64(int N, const int64_t* __restrict__ dfx, const int64_t* __restrict__ hfx,
+                          const float* __restrict__ d, const float* __restrict__ hd, double* __restrict__ d64,
+                          double* __restrict__ h64) {
+  const double unit = 1.0 / (double)(1ull << OBS_FIX_BITS);
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+    if (d64) d64[v] = dfx ? (double)dfx[v] * unit : (double)d[v];
+    if (h64) h64[v] = hfx ? (double)hfx[v] * unit : (double)hd[v];
+  }
+}
+
 __global__ void k_assemble(int N, const uint8_t* __restrict__ info, const float* __restrict__ tsdf,
                            const float* __restrict__ d, const float* __restrict__ hd, float lam, float lamb,
                            float inv_h, float* __restrict__ qd, float* __restrict__ rhs) {
@@ -129,6 +140,17 @@ bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, con
     b->obs_mode = mode;
   }
   return band_assemble(ctx, b);
+}
+
+bf_status band_observations_f64(bf_ctx* ctx, const bf_band* b, double* d64, double* h64) {
+  if (b->N > 0) {
+    const bool fix = b->obs_mode == 2;
+    k_obs_f64<<<grid_for(b->N, 256), 256, 0, ctx->stream>>>((int)b->N, fix ? b->dfx : nullptr, fix ? b->hfx : nullptr,
+                                                            b->d, b->hd, d64, h64);
+    count_launch();
+    BF_CK(cudaGetLastError());
+  }
+  return BF_OK;
 }
 
 bf_status band_assemble(bf_ctx* ctx, bf_band* b) {

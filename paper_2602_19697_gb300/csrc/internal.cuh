@@ -177,7 +177,9 @@ bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, con
                          bool fixed_point = false);
 constexpr int OBS_FIX_BITS = 32;
 bf_status band_assemble(bf_ctx* ctx, bf_band* b);
+bf_status band_observations_f64(bf_ctx* ctx, const bf_band* b, double* d64, double* h64);
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
+bf_status spmm_launch(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y);
 bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,
                           double* relres);
 bf_status solve_rhs_impl(bf_ctx* ctx, bf_band* b, const float* rhs, double tol, int max_iter, float* x, int* iters,

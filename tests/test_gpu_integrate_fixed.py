@@ -60,6 +60,13 @@ def test_fixed_point_sums_are_reproducible_and_match_the_oracle(name):
     gb3.integrate_depth(depth, poses, w.intr)
     s5 = gb3.export_system()
     np.testing.assert_allclose(s5["d"], s1["d"], rtol=1e-5, atol=1e-6 * scale)
+    # FP64 export: the fixed-point totals (rounding them gives the FP32 export), the FP32 sums widened
+    d64, h64 = gb2.export_observations_f64()
+    np.testing.assert_array_equal(d64.astype(np.float32), s3["d"])
+    np.testing.assert_array_equal(h64.astype(np.float32), s3["hdata"])
+    np.testing.assert_allclose(d64, c["d"], rtol=1e-5, atol=1e-7 * scale)
+    d64f, _ = gb3.export_observations_f64()
+    np.testing.assert_array_equal(d64f, s5["d"].astype(np.float64))
 
 
 def test_one_accumulation_mode_per_band_until_reset():

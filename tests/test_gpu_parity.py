@@ -98,6 +98,44 @@ def test_spmv_matches_oracle(name):
     np.testing.assert_array_equal(yh, y.cpu().numpy())
 
 
+@pytest.mark.parametrize("name,R", [("sphere32_small", 8), ("union128", 16), ("blob128_b5", 32), ("sphere64", 32)])
+def test_spmm_matches_oracle_and_the_single_rhs_spmv(name, R):
+    c = case(name)
+    w = c["w"]
+    gb, depth, poses = gpu_band(w)
+    gb.integrate_depth(depth, poses, w.intr)
+    qd32 = gb.export_system()["qdiag"].astype(np.float64)
+    X = np.random.default_rng(R).standard_normal((gb.N, R)).astype(np.float32)
+    X[:, R - 1] = 0.0  # a zero column
+    Y = torch.empty((gb.N, R), device="cuda")
+    gb.spmm(dev(X), Y)
+    Y = Y.cpu().numpy()
+    y1 = torch.empty(gb.N, device="cuda")
+    for col in range(R):
+        ref = oracle.spmv(c["ob"], w.lam, qd32, X[:, col].astype(np.float64))
+        np.testing.assert_allclose(Y[:, col], ref, rtol=0, atol=1e-5 * max(np.abs(ref).max(), 1.0))
+        gb.spmv(dev(np.ascontiguousarray(X[:, col])), y1)
+        np.testing.assert_allclose(Y[:, col], y1.cpu().numpy(), rtol=1e-6, atol=1e-6 * np.abs(Y[:, col]).max())
+    assert np.all(Y[:, R - 1] == 0.0)
+    # host buffers through the same call
+    Yh = np.empty((gb.N, R), np.float32)
+    gb.spmm(X, Yh)
+    np.testing.assert_array_equal(Yh, Y)
+
+
+def test_spmm_argument_checks():
+    c = case("sphere32_small")
+    w = c["w"]
+    gb, depth, poses = gpu_band(w)
+    with pytest.raises(Exception):  # before integration
+        gb.spmm(torch.zeros((gb.N, 8), device="cuda"), torch.empty((gb.N, 8), device="cuda"))
+    gb.integrate_depth(depth, poses, w.intr)
+    with pytest.raises(Exception):
+        gb.spmm(torch.zeros((gb.N, 12), device="cuda"), torch.empty((gb.N, 12), device="cuda"))
+    with pytest.raises(ValueError):
+        gb.spmm(torch.zeros((gb.N, 8), device="cuda"), torch.empty((gb.N, 16), device="cuda"))
+
+
 @pytest.mark.parametrize("name,fp64,tol", [("sphere64", True, 1e-8), ("sphere64", False, 1e-8),
                                            ("union128", False, 1e-8), ("blob128_b5", False, 1e-8),
                                            ("sphere32_small", True, 1e-10), ("sphere32_small", False, 1e-10)])

@@ -25,9 +25,10 @@
 //
 // Refinement: master iterates xm per column in float-float arithmetic (an
 // unevaluated sum hi + lo of two floats, about 48 significant bits: Dekker's
-// exact product by FMA and Knuth's exact sum); k_blk_outer computes the true
-// residual z - Q xm in that arithmetic, the FP32 solve reduces it by a factor
-// eta, xm += x, until every column meets the tolerance.  (FP64 would serve
+// exact product by FMA and Knuth's exact sum); k_blk_res adds the FP32
+// correction x to xm and computes the true residual z - Q xm in that
+// arithmetic, the FP32 solve reduces it by a factor eta, until every column
+// meets the tolerance.  (FP64 would serve
 // too, but its throughput on this GPU is a small fraction of FP32's.)
 //
 // The solver (workspaces, state, graph) belongs to the context, one per
@@ -72,6 +73,7 @@ struct BlkState {
   alignas(16) float aprev[MAXR];
   int xvalid, xpend;
   int want_sq;  // the residual pass also forms the probe values' second moments (hsq)
+  int xmpar;    // which of the double-buffered master iterates is current
   unsigned int cnt, guard;
   unsigned int gcnt[NGRP];  // CTAs of each reduction group that have written their partials
   unsigned int nexec;  // graph-body kernels executed (for launch accounting)
@@ -92,7 +94,7 @@ struct BlkArgs {
   float* s[2];         // Q p (by recurrence)
   float* p;
   float* x;            // FP32 correction
-  float2* xm;          // float-float master iterates (hi, lo)
+  float2* xm[2];       // float-float master iterates (hi, lo), double-buffered ([BlkState::xmpar] is current)
   const __nv_bfloat16* Z;
   double* part;        // [3][R][NCTA]
   double* part1;       // [3][R][NCTA] the iteration's partials (r'.u', r'.r', w'.u')
@@ -218,89 +220,198 @@ __device__ __forceinline__ void load_nb6(const int32_t* __restrict__ nb6, int ro
   nb[0] = n01.x; nb[1] = n01.y; nb[2] = n23.x; nb[3] = n23.y; nb[4] = n45.x; nb[5] = n45.y;
 }
 
-// True residual of the master iterates, per column: r = z - Q xm in
-// float-float arithmetic, stored as the FP32 right-hand side (r[par]) of the
-// next correction solve; per-column r.r and z.z (FP32 products summed per
-// thread, FP64 from the CTA sums on).  The last CTA sets, per column, the
-// stop flag (true residual within tolerance) and the correction target
-// eta = 0.5 tol |z| / |r| clamped to [ETA_MIN, 0.5].
+// One residual pass of the refinement, per tile of SP_TR rows in NP passes of
+// CC columns: the new master iterates xm' = xm + d (d the FP32 correction x,
+// plus the alpha p the last iteration left pending; xm' = d for the block's
+// first correction) of the tile's own rows and of its external face
+// neighbours (the band's gather plan) are formed into shared memory, the own
+// rows' written to the other xm buffer (other CTAs still read the old one);
+// then the true residual r = z - Q xm' in float-float arithmetic, stored as the
+// FP32 right-hand side (r[par]) of the next correction solve, per-column r.r
+// and z.z (FP32 products summed per thread, FP64 from the CTA sums on), and
+// the row's probe sums sum_c z xm', sum_c (z xm')^2 (float-float over the
+// columns, FP64 per row).  The last CTA sets, per column, the stop flag (true
+// residual within tolerance) and the correction target
+// eta = 0.5 tol |z| / |r| clamped to [ETA_MIN, 0.5], and flips xmpar.
 template <int R>
-__global__ void __launch_bounds__(CT, 2) k_blk_outer(const BlkArgs* __restrict__ A, BlkState* st) {
+__global__ void __launch_bounds__(CT, 2) k_blk_res(const BlkArgs* __restrict__ A, BlkState* st, int first) {
+  constexpr int CC = R < 16 ? R : 16;  // columns per pass
+  constexpr int NP = R / CC;           // passes
+  constexpr int F4 = CC / 2;           // float4 (two float2 columns) per row and pass
+  constexpr int RPS = 32 / F4;         // rows per warp step of the stencil phase
+  constexpr int OWN = (SP_TR * F4 + CT - 1) / CT;
+  constexpr int XN = (SP_EMAX * F4 + CT - 1) / CT;
+  static_assert(SP_TR == 16 * (CT / 32) && 16 % RPS == 0 && CT % F4 == 0, "tile / CTA shape");
   const int N = A->N;
   const float lam = A->lam;
-  const int lane = threadIdx.x & 31, c = lane % R;
-  constexpr int RPW = 32 / R;
-  const int wrp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const float2* __restrict__ xm = A->xm;
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5, k2 = threadIdx.x % F4;
+  const int xp = st->xmpar;
   const bool wsq = st->want_sq;
-  int row0, row1;
-  cta_rows(N, &row0, &row1);
-  float fr = 0.0f, fz = 0.0f;
-  // warp-uniform trip count (the per-row sums over the columns below are shuffle trees); each step takes OU
-  // rows per lane group, with the neighbour tables and then all gathers of the OU rows issued before any is used
-  constexpr int OU = 2;
-  for (int base = row0 + wrp * RPW; base < row1; base += OU * nw * RPW) {
-    int rowu[OU], nb[OU][6];
-    bool oku[OU];
+  const float4* __restrict__ xin = reinterpret_cast<const float4*>(A->xm[xp]);
+  float4* __restrict__ xout = reinterpret_cast<float4*>(A->xm[xp ^ 1]);
+  const float2* __restrict__ x2 = reinterpret_cast<const float2*>(A->x);
+  const float2* __restrict__ p2 = reinterpret_cast<const float2*>(A->p);
+  float2* __restrict__ r2 = reinterpret_cast<float2*>(A->r[st->par]);
+  const int xv = st->xvalid, xpd = st->xpend;
+  float ap[NP][2];
 #pragma unroll
-    for (int u = 0; u < OU; ++u) {
-      rowu[u] = base + u * nw * RPW + lane / R;
-      oku[u] = rowu[u] < row1;
-      if (oku[u]) {
-        load_nb6(A->nb6, rowu[u], nb[u]);
-      } else {
+  for (int pp = 0; pp < NP; ++pp) {
+    ap[pp][0] = xpd ? st->aprev[pp * CC + 2 * k2] : 0.f;
+    ap[pp][1] = xpd ? st->aprev[pp * CC + 2 * k2 + 1] : 0.f;
+  }
+  // xm' of this thread's two columns of pass pp in row `row` (the same arithmetic in every CTA)
+  auto upd = [&](int row, int pp) -> float4 {
+    const size_t e = (size_t)row * (R / 2) + pp * F4 + k2;
+    float2 d = xv ? x2[e] : make_float2(0.f, 0.f);
+    if (xpd) {
+      const float2 pv = p2[e];
+      d.x = fmaf(ap[pp][0], pv.x, d.x);
+      d.y = fmaf(ap[pp][1], pv.y, d.y);
+    }
+    if (first) return make_float4(d.x, 0.f, d.y, 0.f);
+    const float4 o = xin[e];
+    const float2 a = ff_add_f(make_float2(o.x, o.y), d.x), b = ff_add_f(make_float2(o.z, o.w), d.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+  };
+  extern __shared__ __align__(16) float4 sx4[];  // [SP_ROWS][F4] staged xm'
+  __shared__ float4 hrow[SP_TR];                 // per own row: probe sums over the passes so far (ff, ff)
+  float fr[NP][2], fz[NP][2];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) nb[u][k] = -1;
+  for (int pp = 0; pp < NP; ++pp) fr[pp][0] = fr[pp][1] = fz[pp][0] = fz[pp][1] = 0.0f;
+  const int ntiles = (N + SP_TR - 1) / SP_TR;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int t0 = tile * SP_TR, t1 = min(N, t0 + SP_TR);
+    const int ne = __ldg(A->sp_ne + tile);
+    const int32_t* __restrict__ ext = A->sp_ext + (size_t)tile * SP_EMAX;
+    uint4 slv = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
+    float qv = 0.0f;
+    {
+      const int myrow = t0 + 16 * wrp + (lane & 15);
+      if (lane < 16 && myrow < t1) {
+        slv = __ldg(reinterpret_cast<const uint4*>(A->sp_slot) + myrow);
+        qv = __ldg(A->qd + myrow);
       }
     }
-    float2 xn[OU][6], xo[OU];
-    float z[OU], q[OU];
+    int ji[XN];
 #pragma unroll
-    for (int u = 0; u < OU; ++u) {
-      const size_t o = (size_t)rowu[u] * R + c;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) xn[u][k] = nb[u][k] >= 0 ? xm[(size_t)nb[u][k] * R + c] : make_float2(0.f, 0.f);
-      xo[u] = oku[u] ? xm[o] : make_float2(0.f, 0.f);
-      z[u] = oku[u] ? __bfloat162float(A->Z[o]) : 0.0f;
-      q[u] = oku[u] ? __ldg(A->qd + rowu[u]) : 0.0f;
+    for (int i = 0; i < XN; ++i) {
+      const int q = threadIdx.x + i * CT;
+      ji[i] = q < SP_EMAX * F4 ? __ldg(ext + q / F4) : 0;
     }
+    const int nown = (t1 - t0) * F4, next = ne * F4;
 #pragma unroll
-    for (int u = 0; u < OU; ++u) {
-      float2 t = make_float2(0.f, 0.f);
-      if (oku[u]) {
-        float2 ns = make_float2(0.f, 0.f);
+    for (int pp = 0; pp < NP; ++pp) {
+      __syncthreads();  // the previous readers of sx4 are done
 #pragma unroll
-        for (int k = 0; k < 6; ++k)
-          if (nb[u][k] >= 0) ns = ff_add(ns, xn[u][k]);
-        const float2 qx = ff_add(ff_mul_f(xo[u], q[u]), ff_neg(ff_mul_f(ns, lam)));
-        const float2 rf = ff_add_f(ff_neg(qx), z[u]);
-        const float r = __fadd_rn(rf.x, rf.y);
-        A->r[st->par][(size_t)rowu[u] * R + c] = r;
-        fr += r * r;
-        fz += z[u] * z[u];
-        t = make_float2(z[u] * xo[u].x, z[u] * xo[u].y);  // z = +-1 or 0: exact
-      }
-      // probe sums of this row (kept by the last residual pass of the block): float-float tree over the
-      // columns in a fixed order, then FP64
-      float2 qq = make_float2(0.f, 0.f);
-      if (wsq) {
-        const float p0 = __fmul_rn(t.x, t.x);
-        qq = quick_two_sum(p0, __fmaf_rn(2.0f * t.x, t.y, __fmaf_rn(t.x, t.x, -p0)));
+      for (int i = 0; i < OWN; ++i) {
+        const int q = threadIdx.x + i * CT;
+        if (q < nown) {
+          const int row = t0 + q / F4;
+          const float4 v = upd(row, pp);
+          sx4[q] = v;
+          xout[(size_t)row * (R / 2) + pp * F4 + k2] = v;
+        }
       }
 #pragma unroll
-      for (int o = R / 2; o > 0; o >>= 1) {
-        t = ff_add(t, make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o)));
-        if (wsq)
-          qq = ff_add(qq, make_float2(__shfl_xor_sync(0xffffffffu, qq.x, o), __shfl_xor_sync(0xffffffffu, qq.y, o)));
+      for (int i = 0; i < XN; ++i) {
+        const int q = threadIdx.x + i * CT;
+        if (q < next) sx4[SP_TR * F4 + q] = upd(ji[i], pp);
       }
-      if (oku[u] && c == 0) {
-        A->hsum[rowu[u]] = (double)t.x + (double)t.y;
-        if (wsq) A->hsq[rowu[u]] = (double)qq.x + (double)qq.y;
+      __syncthreads();
+#pragma unroll 1
+      for (int jstep = 0; jstep < 16 / RPS; ++jstep) {
+        const int src = jstep * RPS + lane / F4;  // row of the warp's 16, and the lane holding its slots
+        const int rr = 16 * wrp + src, row = t0 + rr;
+        const uint32_t sx = __shfl_sync(0xffffffffu, slv.x, src), sy = __shfl_sync(0xffffffffu, slv.y, src),
+                       sz = __shfl_sync(0xffffffffu, slv.z, src);
+        const float q = __shfl_sync(0xffffffffu, qv, src);
+        const bool ok = row < t1;
+        float2 t = make_float2(0.f, 0.f), qq = make_float2(0.f, 0.f);
+        if (ok) {
+          const int sv[6] = {(int16_t)(sx & 0xffffu), (int16_t)(sx >> 16), (int16_t)(sy & 0xffffu),
+                             (int16_t)(sy >> 16),     (int16_t)(sz & 0xffffu), (int16_t)(sz >> 16)};
+          const float4 xo = sx4[rr * F4 + k2];
+          float2 n0 = make_float2(0.f, 0.f), n1 = n0;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const int sk = sv[k];
+            if (sk < 0) continue;
+            const float4 v = sk == SP_GLOBAL ? upd(__ldg(A->nb6 + 6 * (size_t)row + k), pp) : sx4[sk * F4 + k2];
+            n0 = ff_add(n0, make_float2(v.x, v.y));
+            n1 = ff_add(n1, make_float2(v.z, v.w));
+          }
+          const int c0 = pp * CC + 2 * k2;
+          const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162*>(A->Z + (size_t)row * R + c0);
+          const float z0 = __low2float(zz), z1 = __high2float(zz);
+          const float2 xo0 = make_float2(xo.x, xo.y), xo1 = make_float2(xo.z, xo.w);
+          const float2 qx0 = ff_add(ff_mul_f(xo0, q), ff_neg(ff_mul_f(n0, lam)));
+          const float2 qx1 = ff_add(ff_mul_f(xo1, q), ff_neg(ff_mul_f(n1, lam)));
+          const float2 rf0 = ff_add_f(ff_neg(qx0), z0), rf1 = ff_add_f(ff_neg(qx1), z1);
+          const float ra = __fadd_rn(rf0.x, rf0.y), rb = __fadd_rn(rf1.x, rf1.y);
+          r2[((size_t)row * R + c0) / 2] = make_float2(ra, rb);
+          fr[pp][0] += ra * ra;
+          fr[pp][1] += rb * rb;
+          fz[pp][0] += z0 * z0;
+          fz[pp][1] += z1 * z1;
+          const float2 t0v = make_float2(z0 * xo0.x, z0 * xo0.y), t1v = make_float2(z1 * xo1.x, z1 * xo1.y);  // exact
+          t = ff_add(t0v, t1v);
+          if (wsq) {
+            const float pa = __fmul_rn(t0v.x, t0v.x), pb = __fmul_rn(t1v.x, t1v.x);
+            qq = ff_add(quick_two_sum(pa, __fmaf_rn(2.0f * t0v.x, t0v.y, __fmaf_rn(t0v.x, t0v.x, -pa))),
+                        quick_two_sum(pb, __fmaf_rn(2.0f * t1v.x, t1v.y, __fmaf_rn(t1v.x, t1v.x, -pb))));
+          }
+        }
+        // the row's probe sums over its column pairs (lanes of the row), then over the passes
+#pragma unroll
+        for (int o = F4 / 2; o > 0; o >>= 1) {
+          t = ff_add(t, make_float2(__shfl_xor_sync(0xffffffffu, t.x, o), __shfl_xor_sync(0xffffffffu, t.y, o)));
+          if (wsq)
+            qq = ff_add(qq, make_float2(__shfl_xor_sync(0xffffffffu, qq.x, o), __shfl_xor_sync(0xffffffffu, qq.y, o)));
+        }
+        if (ok && k2 == 0) {
+          if (pp > 0) {
+            const float4 h = hrow[rr];
+            t = ff_add(make_float2(h.x, h.y), t);
+            qq = ff_add(make_float2(h.z, h.w), qq);
+          }
+          if (pp + 1 < NP) {
+            hrow[rr] = make_float4(t.x, t.y, qq.x, qq.y);
+          } else {
+            A->hsum[row] = (double)t.x + (double)t.y;
+            if (wsq) A->hsq[row] = (double)qq.x + (double)qq.y;
+          }
+        }
       }
     }
   }
-  double acc[2] = {(double)fr, (double)fz};
-  column_partials<R, 2>(acc, A->part);
+  // per-column CTA sums (lanes sharing threadIdx % F4, then warps) -> part[q][c][CTA], q: 0 = r.r, 1 = z.z
+  {
+    constexpr int NA = 2 * NP * 2;
+    __shared__ double shr[CT / 32][F4][NA];
+    double acc[NA];
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        acc[(0 * NP + pp) * 2 + j] = (double)fr[pp][j];
+        acc[(1 * NP + pp) * 2 + j] = (double)fz[pp][j];
+      }
+#pragma unroll
+    for (int k = 0; k < NA; ++k)
+      for (int o = 16; o >= F4; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (lane < F4) {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) shr[wrp][lane][k] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * R) {
+      const int qk = threadIdx.x / R, cc = threadIdx.x % R;
+      const int pp = cc / CC, kk = (cc % CC) / 2, j = cc & 1;
+      double tsum = 0.0;
+      for (int ww = 0; ww < CT / 32; ++ww) tsum += shr[ww][kk][(qk * NP + pp) * 2 + j];
+      A->part[((size_t)qk * R + cc) * NCTA + blockIdx.x] = tsum;
+    }
+  }
   __shared__ double tot[3][MAXR];
   if (!reduce_partials<2>(A->part, A->gpart, st, R, tot)) return;
   if (threadIdx.x < R) {
@@ -323,6 +434,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_outer(const BlkArgs* __restrict__
     if (!all && st->iter >= st->max_iter) st->status = 1;
     st->all_done = all || st->iter >= st->max_iter || st->status == 2;
     st->first = 1;
+    st->xmpar ^= 1;
     st->cnt = 0;
     st->guard = 0;
   }
@@ -749,19 +861,6 @@ __global__ void k_finish(int N, const double* __restrict__ sacc, double invK, fl
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) s[i] = (float)(sacc[i] * invK);
 }
 
-// xm += d in float-float arithmetic (xm = d for the first correction of a block), d the correction:
-// x (when it holds a value) plus the alpha p left pending by the last iteration
-template <int R>
-__global__ void k_axpy_ff(int64_t n, const BlkState* __restrict__ st, const float* __restrict__ x,
-                          const float* __restrict__ p, float2* __restrict__ xm, int first) {
-  const int xv = st->xvalid, xp = st->xpend;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float d = xv ? x[i] : 0.0f;
-    if (xp) d = fmaf(st->aprev[i % R], p[i], d);
-    xm[i] = first ? make_float2(d, 0.0f) : ff_add_f(xm[i], d);
-  }
-}
-
 // s_acc += hsum, sq += hsq (the block's probe sums from its last residual pass)
 __global__ void k_hadd(int N, const double* __restrict__ hsum, const double* __restrict__ hsq, double* __restrict__ sacc,
                        double* __restrict__ sq) {
@@ -900,6 +999,7 @@ __global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, in
     st->status = 0;
     st->ncols = ncols;
     st->want_sq = want_sq;
+    st->xmpar = 0;
     st->first = 1;
     st->par = 0;  // k_probes wrote the first right-hand side into r[0]
     st->cnt = 0;
@@ -949,7 +1049,7 @@ struct BlockGraph {
 
 static void free_arrays(BlockGraph* g) {
   void* ptrs[] = {g->h.r[0], g->h.w[0], g->h.s[0], g->h.r[1], g->h.w[1], g->h.s[1], g->h.p, g->h.x,
-                  g->h.xm, g->h.iq,       g->h.part, g->h.part1, g->Z, g->sacc, g->h.hsum, g->h.hsq, g->h.gpart};
+                  g->h.xm[0], g->h.xm[1], g->h.iq,       g->h.part, g->h.part1, g->Z, g->sacc, g->h.hsum, g->h.hsq, g->h.gpart};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   g->cap_rows = 0;
@@ -980,9 +1080,13 @@ static void blk_start(BlockGraph* g, cudaStream_t s) {
   count_launch();
 }
 
+// shared memory of the residual pass: the staged master iterates of a tile (16 columns at a time)
+constexpr size_t res_smem(int R) { return (size_t)SP_ROWS * (R < 16 ? R : 16) / 2 * sizeof(float4); }
+
+// xm += correction, true residual, stop test; then the start of the next correction solve
 template <int R>
-static void blk_outer(BlockGraph* g, cudaStream_t s) {
-  k_blk_outer<R><<<NCTA, CT, 0, s>>>(g->d_args, g->st);
+static void blk_outer(BlockGraph* g, cudaStream_t s, bool first) {
+  k_blk_res<R><<<NCTA, CT, res_smem(R), s>>>(g->d_args, g->st, first ? 1 : 0);
   count_launch();
   blk_start<R>(g, s);
 }
@@ -1022,6 +1126,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     g->R = R;
     BF_CK(cudaFuncSetAttribute(k_blk_it<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
     BF_CK(cudaFuncSetAttribute(k_blk_it<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
+    BF_CK(cudaFuncSetAttribute(k_blk_res<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem(R)));
     memset(&g->h, 0, sizeof(g->h));
     BF_CK(cudaMalloc(&g->d_args, sizeof(BlkArgs)));
     BF_CK(cudaMallocHost(&g->h_pin, sizeof(BlkArgs)));
@@ -1061,7 +1166,8 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     }
     BF_CK(cudaMalloc(&g->h.p, nv * 4));
     BF_CK(cudaMalloc(&g->h.x, nv * 4));
-    BF_CK(cudaMalloc(&g->h.xm, nv * sizeof(float2)));
+    BF_CK(cudaMalloc(&g->h.xm[0], nv * sizeof(float2)));
+    BF_CK(cudaMalloc(&g->h.xm[1], nv * sizeof(float2)));
     BF_CK(cudaMalloc(&g->h.hsum, (size_t)rows * sizeof(double)));
     BF_CK(cudaMalloc(&g->h.hsq, (size_t)rows * sizeof(double)));
     BF_CK(cudaMalloc(&g->Z, nv * 2));
@@ -1128,9 +1234,7 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
         break;
       }
       BF_CK(cudaGraphLaunch(g->exec, s));
-      k_axpy_ff<R><<<gNR, 256, 0, s>>>(NR, g->st, g->h.x, g->h.p, g->h.xm, nouter == 0);
-      count_launch();
-      blk_outer<R>(g, s);
+      blk_outer<R>(g, s, nouter == 0);
       ++nouter;
       BF_CK(cudaGetLastError());
     }

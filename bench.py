@@ -176,6 +176,12 @@ def oracle_sample(w, system, tol, K, budget_s, k0=0):
     return est, cores, sample, k
 
 
+def workload_desc(w, args):
+    """The workload string of the bench line's config (both arms)."""
+    return (f"{w.name}: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, "
+            f"{w.T} views {w.intr[4]}x{w.intr[5]}, K={args.K} probes, rel_tol {args.tol:g}")
+
+
 def run_reference(args, world, rank):
     """The CPU oracle as the reference arm: each step times a bounded sample
     of the posterior solve on the host cores (rank 0 only)."""
@@ -195,7 +201,7 @@ def run_reference(args, world, rank):
     line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": w.name, "K": args.K, "rel_tol": args.tol},
+            "config": {"workload": workload_desc(w, args), "parallelism": f"replicas x{world}"},
             "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -359,8 +365,7 @@ def run_ours(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{w.name}: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, "
-                                       f"{w.T} views {w.intr[4]}x{w.intr[5]}, K={args.K} probes, rel_tol {args.tol:g}",
+                "config": {"workload": workload_desc(w, args),
                            "N_band": info["N"], "bricks": info["NB"], "rhs_block": R_used,
                            "rhs_block_choice": "autotuned" if not R else "fixed",
                            "autotune_ms_per_iter_r8_r16_r32": None if tune_ms is None else [round(float(v), 5) for v in tune_ms],

@@ -1227,24 +1227,24 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
     bool done = false;
     int nouter = 0;  // residual passes run (the last one leaves the block's probe sums in hsum, hsq)
     for (int outer = 0; outer < 64; ++outer) {
+      // correction solve (its first kernel ends the loop at once if the state is already final), then the
+      // residual pass and the next start; the host looks at the state only after each residual pass
+      BF_CK(cudaGraphLaunch(g->exec, s));
+      blk_outer<R>(g, s, nouter == 0);
+      ++nouter;
+      BF_CK(cudaGetLastError());
       BF_CK(cudaMemcpyAsync(g->h_st, g->st, sizeof(BlkState), cudaMemcpyDeviceToHost, s));
       BF_CK(cudaStreamSynchronize(s));
       if (g->h_st->all_done) {
         done = true;
         break;
       }
-      BF_CK(cudaGraphLaunch(g->exec, s));
-      blk_outer<R>(g, s, nouter == 0);
-      ++nouter;
-      BF_CK(cudaGetLastError());
     }
     const BlkState& h = *g->h_st;
     count_launch(h.nexec);
     for (int c = 0; c < ncols; ++c) tot_it += h.iters[c];
-    if (nouter > 0) {
-      k_hadd<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->h.hsum, g->h.hsq, g->sacc, sq);
-      count_launch();
-    }
+    k_hadd<<<grid_for(N, 256, 152 * 16), 256, 0, s>>>(N, g->h.hsum, g->h.hsq, g->sacc, sq);
+    count_launch();
     BF_CK(cudaGetLastError());
     if (h.status == 2) { result = BF_BREAKDOWN; break; }
     if (!done || h.status == 1) { result = BF_NOT_CONVERGED; break; }

@@ -181,44 +181,6 @@ __device__ __forceinline__ bool reduce_partials(const double* part, double* gpar
   return true;
 }
 
-// per-column CTA sums of NV values held one column per lane (lane % R) ->
-// part[k][c][blockIdx.x]
-template <int R, int NV>
-__device__ __forceinline__ void column_partials(double (&v)[NV], double* part) {
-  __shared__ double sh[CT / 32][NV][MAXR];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k)
-#pragma unroll
-    for (int o = 16; o >= R; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  if (lane < R) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sh[w][k][lane] = v[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < NV * R) {
-    const int k = threadIdx.x / R, c = threadIdx.x % R;
-    double s = 0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q][k][c];
-    part[((size_t)k * R + c) * NCTA + blockIdx.x] = s;
-    __threadfence();
-  }
-}
-
-// rows [row0, row1) of this CTA: contiguous slices, so a brick and most of its
-// face neighbours are handled by the same CTA (L1 reuse of neighbour rows)
-__device__ __forceinline__ void cta_rows(int N, int* row0, int* row1) {
-  int per = (N + gridDim.x - 1) / gridDim.x;
-  *row0 = min(N, (int)blockIdx.x * per);
-  *row1 = min(N, *row0 + per);
-}
-
-__device__ __forceinline__ void load_nb6(const int32_t* __restrict__ nb6, int row, int nb[6]) {
-  const int2 n01 = __ldg((const int2*)(nb6 + 6 * (size_t)row));
-  const int2 n23 = __ldg((const int2*)(nb6 + 6 * (size_t)row + 2));
-  const int2 n45 = __ldg((const int2*)(nb6 + 6 * (size_t)row + 4));
-  nb[0] = n01.x; nb[1] = n01.y; nb[2] = n23.x; nb[3] = n23.y; nb[4] = n45.x; nb[5] = n45.y;
-}
 
 // One residual pass of the refinement, per tile of SP_TR rows in NP passes of
 // CC columns: the new master iterates xm' = xm + d (d the FP32 correction x,

@@ -329,6 +329,30 @@ def score_views(band: Band, mu, s, qdiag, cand_poses, cand_intr, band_vox, sig_a
     return U, best
 
 
+def score_views_exact(band: Band, mu, qdiag, lam, cand_poses, cand_intr, band_vox, sig_a, sig_b, K, seed,
+                      tol=1e-12, sig_pose=0.0, sig_model=0.0, eps=1.0):
+    """Exact view utilities (the re-solve the NBV equation's s' stands for, Sec. 3.8): per candidate v the
+    predicted observations dd_v of its predicted depth (``predict_depth`` then ``integrate``) are added to the
+    diagonal of Q and the K-probe estimate is recomputed with the same probes:
+    U[v] = sum_{|mu_j| <= eps} (s_j - s'_j).  Returns (U f64 [V], best)."""
+    mu32 = _f32(mu)
+    qdiag = _f64(qdiag)
+    s, st, _, _ = hutchinson(band, lam, qdiag, K, seed, tol=tol)
+    if st != 0:
+        raise RuntimeError("hutchinson did not converge")
+    om = np.abs(mu32.astype(np.float64)) <= eps
+    cand = _f32(cand_poses)
+    U = np.zeros(cand.shape[0], np.float64)
+    for v in range(cand.shape[0]):
+        Dp = predict_depth(band, mu32, cand[v], cand_intr)
+        dd, _, _ = integrate(band, Dp[None], cand[v:v + 1], cand_intr, band_vox, sig_a, sig_b, sig_pose, sig_model)
+        s2, st, _, _ = hutchinson(band, lam, qdiag + dd, K, seed, tol=tol)
+        if st != 0:
+            raise RuntimeError("hutchinson did not converge")
+        U[v] = float(np.sum((s - s2)[om]))
+    return U, int(np.argmax(U))
+
+
 def solve_all(w, threads=0, tol=1e-12, K=None):
     """Full oracle pipeline for a workload: band, d/h, Q, mu and (optionally) s."""
     b = build_band_w(w, threads)

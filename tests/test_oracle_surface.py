@@ -180,3 +180,42 @@ def test_view_that_sees_no_band_scores_zero_and_utilities_are_nonnegative():
     U, best = oracle.score_views(b, mu32, r["s"], r["qdiag"], cand, w.cand_intr, w.band_vox, w.sig_a, w.sig_b)
     assert U[0] == 0.0
     assert np.all(U >= 0) and U.max() > 0 and best == int(np.argmax(U))
+
+
+def test_exact_utility_without_prior_is_the_closed_form_variance_reduction(sphere_views):
+    """lambda = 0: Q diagonal, one Rademacher probe gives diag(Q^-1) exactly (z^2 = 1), so the exact utility is
+    sum (1/Q_ii - 1/(Q_ii + dd_i)) over the near-surface voxels, which the diagonal update also equals."""
+    w, b = sphere_views
+    d, hd, _ = oracle.integrate_w(b, w)
+    qd, rhs = oracle.assemble(b, d, hd, 0.0, 1.0)
+    qd = qd + 1e-3
+    mu, *_ = oracle.pcg(b, 0.0, qd, rhs, tol=1e-13)
+    mu32 = mu.astype(np.float32)
+    cand = w.cand_poses[:3]
+    U, best = oracle.score_views_exact(b, mu32, qd, 0.0, cand, w.cand_intr, w.band_vox, w.sig_a, w.sig_b, K=1,
+                                       seed=4, tol=1e-13)
+    om = np.abs(mu32.astype(np.float64)) <= 1.0
+    s = 1.0 / qd
+    Ud, _ = oracle.score_views(b, mu32, s, qd, cand, w.cand_intr, w.band_vox, w.sig_a, w.sig_b)
+    for v in range(len(cand)):
+        Dp = oracle.predict_depth(b, mu32, cand[v], w.cand_intr)
+        dd, _, _ = oracle.integrate(b, Dp[None], cand[v:v + 1], w.cand_intr, w.band_vox, w.sig_a, w.sig_b)
+        ref = np.sum((1.0 / qd - 1.0 / (qd + dd))[om])
+        assert abs(U[v] - ref) <= 1e-9 * max(ref, 1e-30)
+        assert abs(U[v] - Ud[v]) <= 1e-9 * max(ref, 1e-30)
+    assert best == int(np.argmax(U))
+
+
+def test_exact_utility_with_prior_is_positive_and_below_the_prior_variance_sum(sphere_views):
+    """With the prior, adding precision can only lower the exact marginal variances (Q' >= Q), so with the same
+    probes the estimate drops on average: U > 0 for a view that sees the surface, and U < sum s over the set."""
+    w, b = sphere_views
+    d, hd, _ = oracle.integrate_w(b, w)
+    qd, rhs = oracle.assemble(b, d, hd, w.lam, w.lam_b)
+    mu, *_ = oracle.pcg(b, w.lam, qd, rhs, tol=1e-12)
+    mu32 = mu.astype(np.float32)
+    s, *_ = oracle.hutchinson(b, w.lam, qd, 16, 1, tol=1e-12)
+    U, _ = oracle.score_views_exact(b, mu32, qd, w.lam, w.cand_poses[:2], w.cand_intr, w.band_vox, w.sig_a,
+                                    w.sig_b, K=16, seed=1, tol=1e-12)
+    om = np.abs(mu32.astype(np.float64)) <= 1.0
+    assert np.all(U > 0) and np.all(U < np.sum(s[om]))

@@ -229,6 +229,21 @@ bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris);
 bf_status bf_score_views(bf_ctx* ctx, const bf_band* band, const float* mu, const float* s,
                          const float* cand_poses, int V, const bf_intrinsics* K, double eps, double* U, int* best);
 
+/* Exact view utilities: the marginal variances after a candidate's
+ * observations re-estimated instead of approximated by the diagonal update
+ * (s' of the Sec. 3.8 NBV equation).  For each candidate v the predicted
+ * precision dd_v (as in bf_score_views) is added to the diagonal of Q and the
+ * K_probes-probe estimate (seed, rel_tol, max_iter, rhs_block as in
+ * bf_estimate_variance) is recomputed with the same probes;
+ * U(v) = sum_{|mu_j| <= eps} (s_j - s'_j), s the estimate under Q with those
+ * probes.  Costs V + 1 variance estimates.  mu [N] float (voxels);
+ * U [V] double (host or device); *best (host, may be NULL) = argmax, lowest
+ * index on ties; *total_iters (host, may be NULL) = probe iterations summed.
+ * Errors as bf_estimate_variance and bf_score_views. */
+bf_status bf_score_views_exact(bf_ctx* ctx, bf_band* band, const float* mu, const float* cand_poses, int V,
+                               const bf_intrinsics* K, double eps, int K_probes, uint64_t seed, double rel_tol,
+                               int max_iter, int rhs_block, double* U, int* best, int* total_iters);
+
 /* Autotuner of the probe block width (the library choice rhs_block = 0 of
  * bf_estimate_variance uses it): times one block-PCG iteration on this band
  * at R = 8, 16, 32 (R not wider than K needs) and returns the R that

@@ -33,7 +33,7 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_reset_observations",
             "bf_export_system",
             "bf_spmv", "bf_spmm", "bf_solve_mean", "bf_estimate_variance", "bf_extract_surface", "bf_get_surface",
-            "bf_score_views", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
+            "bf_score_views", "bf_score_views_exact", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
             "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
             "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance",
             "bf_net_bench", "bf_autotune_rhs_block"]
@@ -104,6 +104,8 @@ def load_library(path: str = LIB_PATH):
         "bf_extract_surface": (i, [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "bf_get_surface": (i, [vp, vp, vp]),
         "bf_score_views": (i, [vp, vp, vp, vp, vp, i, ctypes.POINTER(Intrinsics), d, vp, ctypes.POINTER(i)]),
+        "bf_score_views_exact": (i, [vp, vp, vp, vp, i, ctypes.POINTER(Intrinsics), d, i, ctypes.c_uint64, d, i, i,
+                                     vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "bf_solve_mean_static": (i, [vp, vp, d, i, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "bf_estimate_variance_range": (i, [vp, vp, i, i, ctypes.c_uint64, d, i, i, u, vp, ctypes.POINTER(i)]),
         "bf_bench_kernel": (i, [vp, vp, i, i, i, ctypes.POINTER(d)]),
@@ -356,6 +358,19 @@ class Band:
                                                    ctypes.byref(_intr(K)), float(eps), _ptr(U),
                                                    ctypes.byref(best)), "bf_score_views")
         return U, best.value
+
+    def score_views_exact(self, mu, cand_poses, K, eps=1.0, K_probes=16, seed=0, rel_tol=1e-6, max_iter=20000,
+                          rhs_block=0):
+        """Exact utilities (bf_score_views_exact): returns (U [V] float64, best, total probe iterations)."""
+        V = int(cand_poses.shape[0])
+        U = np.zeros(V, np.float64)
+        best, it = ctypes.c_int(), ctypes.c_int()
+        self.ctx.check(self.ctx.lib.bf_score_views_exact(self.ctx._p, self._p, _ptr(mu), _ptr(cand_poses), V,
+                                                         ctypes.byref(_intr(K)), float(eps), int(K_probes),
+                                                         int(seed), float(rel_tol), int(max_iter), int(rhs_block),
+                                                         _ptr(U), ctypes.byref(best), ctypes.byref(it)),
+                       "bf_score_views_exact")
+        return U, best.value, it.value
 
     def bench_kernel(self, which: int, R: int = 32, reps: int = 50) -> float:
         """Mean ms per launch of one solver kernel (bf_bench_kernel)."""

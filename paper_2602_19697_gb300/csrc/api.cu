@@ -416,6 +416,23 @@ bf_status bf_score_views(bf_ctx* ctx, const bf_band* b, const float* mu, const f
   return nbv_impl(ctx, b, dmu, ds, dc, V, to_intr(K), eps, U, best);
 }
 
+bf_status bf_score_views_exact(bf_ctx* ctx, bf_band* b, const float* mu, const float* cand, int V,
+                               const bf_intrinsics* K, double eps, int K_probes, uint64_t seed, double rel_tol,
+                               int max_iter, int rhs_block, double* U, int* best, int* total_iters) {
+  if (!ctx || !b || !mu || !cand || !U || V < 1 || !valid_intr(K) || !(eps >= 0.0) || K_probes < 1 ||
+      !(rel_tol > 0.0) || max_iter < 1)
+    return bf_fail(ctx, BF_EINVAL, "bf_score_views_exact: null pointer, V < 1, K < 1, eps < 0, rel_tol <= 0, "
+                                   "max_iter < 1 or bad intrinsics");
+  if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
+    return bf_fail(ctx, BF_EINVAL, "bf_score_views_exact: rhs_block must be 0, 1, 8, 16 or 32");
+  if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_score_views_exact: call bf_integrate_depth first");
+  const float *dmu, *dc;
+  BF_TRY(stage_in(ctx, mu, b->N, WS_STAGE2, &dmu));
+  BF_TRY(stage_in(ctx, cand, (size_t)V * 12, WS_STAGE1, &dc));
+  return nbv_exact_impl(ctx, b, dmu, dc, V, to_intr(K), eps, K_probes, seed, rel_tol, max_iter, rhs_block, U, best,
+                        total_iters);
+}
+
 bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms_per_launch) {
   if (!ctx || !b || !ms_per_launch || reps < 1 || reps > 100000) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_bench_kernel: call bf_integrate_depth first");

@@ -188,6 +188,32 @@ __global__ void __launch_bounds__(RT) k_nbv_util(int N, const float* __restrict_
   }
 }
 
+// Q_jj + dd_j: the diagonal after the candidate's predicted observations
+__global__ void k_qd_plus(int N, const float* __restrict__ qd, const float* __restrict__ dd, float* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) out[i] = qd[i] + dd[i];
+}
+
+// per-CTA FP64 partials of sum_{|mu_j| <= eps} (s_j - s'_j) for candidate v -> part[v][CTA]
+__global__ void __launch_bounds__(RT) k_nbv_exact(int N, const float* __restrict__ mu, const float* __restrict__ s,
+                                                  const float* __restrict__ s2, float eps, int v,
+                                                  double* __restrict__ part) {
+  double acc = 0.0;
+  for (int i = blockIdx.x * RT + threadIdx.x; i < N; i += gridDim.x * RT) {
+    if (!(fabsf(__ldg(mu + i)) <= eps)) continue;
+    acc += (double)__ldg(s + i) - (double)__ldg(s2 + i);
+  }
+  __shared__ double sh[RT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < RT / 32; ++w) t += sh[w];
+    part[(int64_t)v * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 __global__ void k_nbv_sum(const double* __restrict__ part, int nblk, int V, double* __restrict__ U) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= V) return;
@@ -197,6 +223,85 @@ __global__ void k_nbv_sum(const double* __restrict__ part, int nblk, int V, doub
 }
 
 }  // namespace
+
+// the candidates' predicted observations dd [V][N] (zeroed first)
+static void nbv_observations(bf_ctx* ctx, const bf_band* b, const float* mu, const float* cand, int V, const Intr& K,
+                             float* dd) {
+  cudaStream_t st_ = ctx->stream;
+  const int64_t N = b->N;
+  cudaMemsetAsync(dd, 0, (size_t)V * N * 4, st_);
+  const bf_params& p = b->prm;
+  float tau = (float)p.band_vox * b->grid.voxel;
+  float s2x = (float)(p.sig_pose * p.sig_pose + p.sig_model * p.sig_model);
+  int64_t n = (int64_t)V * K.W * K.H;
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 64) g = 152 * 64;
+  k_nbv_obs<<<(unsigned)g, 256, 0, st_>>>(band_view(b), mu, cand, V, K, tau, dda_max_steps(p.band_vox),
+                                         (float)p.sig_a, (float)p.sig_b, s2x, dd, nullptr);
+  count_launch();
+}
+
+// U [V] from the device copy dU: argmax and the copy to the caller's buffer
+static bf_status nbv_finish(bf_ctx* ctx, const double* dU, int V, double* U, int* best) {
+  cudaStream_t st_ = ctx->stream;
+  std::vector<double> hU(V);
+  BF_CK(cudaMemcpyAsync(hU.data(), dU, (size_t)V * 8, cudaMemcpyDeviceToHost, st_));
+  BF_CK(cudaStreamSynchronize(st_));
+  int bi = 0;
+  for (int v = 1; v < V; ++v)
+    if (hU[v] > hU[bi]) bi = v;
+  if (best) *best = bi;
+  if (is_device_ptr(U)) BF_CK(cudaMemcpyAsync(U, dU, (size_t)V * 8, cudaMemcpyDeviceToDevice, st_));
+  else memcpy(U, hU.data(), (size_t)V * 8);
+  return BF_OK;
+}
+
+bf_status nbv_exact_impl(bf_ctx* ctx, bf_band* b, const float* mu, const float* cand, int V, const Intr& K,
+                         double eps, int Kp, uint64_t seed, double tol, int max_iter, int R, double* U, int* best,
+                         int* total_iters) {
+  cudaStream_t st_ = ctx->stream;
+  const int64_t N = b->N;
+  bf_status st;
+  const int nblk = 152 * 2;
+  float* dd = (float*)ws_get(ctx, WS_TMP0, (size_t)V * (N ? N : 1) * 4, &st);
+  if (st) return st;
+  double* part = (double*)ws_get(ctx, WS_TMP1, (size_t)V * nblk * 8 + (size_t)V * 8, &st);
+  if (st) return st;
+  float* qd2 = (float*)ws_get(ctx, WS_TMP2, (size_t)(N ? N : 1) * 4, &st);
+  if (st) return st;
+  float* s0 = (float*)ws_get(ctx, WS_TMP3, (size_t)(N ? N : 1) * 4, &st);
+  if (st) return st;
+  float* s2 = (float*)ws_get(ctx, WS_TMP4, (size_t)(N ? N : 1) * 4, &st);
+  if (st) return st;
+  double* dU = part + (size_t)V * nblk;
+  int tot = 0;
+  if (N > 0) {
+    nbv_observations(ctx, b, mu, cand, V, K, dd);
+    int it = 0;
+    BF_TRY(variance_impl(ctx, b, 0, Kp, 1.0 / Kp, seed, tol, max_iter, R, 0u, s0, &it));
+    tot += it;
+    float* const qd0 = b->qd;
+    for (int v = 0; v < V; ++v) {
+      k_qd_plus<<<(unsigned)((N + 255) / 256 < 152 * 16 ? (N + 255) / 256 : 152 * 16), 256, 0, st_>>>(
+          (int)N, qd0, dd + (size_t)v * N, qd2);
+      count_launch();
+      b->qd = qd2;  // the band's diagonal with the candidate's precision, for this estimate only
+      st = variance_impl(ctx, b, 0, Kp, 1.0 / Kp, seed, tol, max_iter, R, 0u, s2, &it);
+      b->qd = qd0;
+      if (st) return st;
+      tot += it;
+      k_nbv_exact<<<nblk, RT, 0, st_>>>((int)N, mu, s0, s2, (float)eps, v, part);
+      count_launch();
+    }
+    k_nbv_sum<<<(V + 127) / 128, 128, 0, st_>>>(part, nblk, V, dU);
+    count_launch();
+    BF_CK(cudaGetLastError());
+  } else {
+    BF_CK(cudaMemsetAsync(dU, 0, (size_t)V * 8, st_));
+  }
+  if (total_iters) *total_iters = tot;
+  return nbv_finish(ctx, dU, V, U, best);
+}
 
 bf_status nbv_impl(bf_ctx* ctx, const bf_band* b, const float* mu, const float* s, const float* cand, int V,
                    const Intr& K, double eps, double* U, int* best) {

@@ -262,6 +262,31 @@ def test_view_scores_match_oracle(name):
     assert best == besto or Uo[best] >= Uo[besto] * (1 - 1e-3)
 
 
+@pytest.mark.parametrize("name,R", [("sphere32_small", 8), ("union128", 0)])
+def test_exact_view_utilities_match_oracle(name, R):
+    c = case(name)
+    w = c["w"]
+    gb, depth, poses = gpu_band(w)
+    gb.integrate_depth(depth, poses, w.intr)
+    mu32 = c["mu"].astype(np.float32)
+    cand = w.cand_poses[:3]
+    K, seed = 8, 2
+    U, best, iters = gb.score_views_exact(dev(mu32), dev(cand), w.cand_intr, K_probes=K, seed=seed, rel_tol=1e-10,
+                                          rhs_block=R)
+    Uo, besto = oracle.score_views_exact(c["ob"], mu32, c["qd"], w.lam, cand, w.cand_intr, w.band_vox, w.sig_a,
+                                         w.sig_b, K=K, seed=seed, tol=1e-12, sig_pose=w.sig_pose,
+                                         sig_model=w.sig_model)
+    assert Uo.max() > 0 and iters > 0
+    np.testing.assert_allclose(U, Uo, rtol=1e-3, atol=1e-5 * np.abs(Uo).max())
+    assert best == besto or Uo[best] >= Uo[besto] * (1 - 1e-3)
+    # the band's own diagonal is left as it was
+    s1 = torch.empty(gb.N, device="cuda")
+    gb.estimate_variance(s1, K=K, seed=seed, rel_tol=1e-10, rhs_block=R)
+    so, *_ = oracle.hutchinson(c["ob"], w.lam, c["qd"], K, seed, tol=1e-12)
+    rel = np.abs(s1.cpu().numpy() - so) / np.maximum(np.abs(so), 1.0 / c["qd"])
+    assert rel.max() <= VAR_TOL_REL
+
+
 def test_probe_ranges_sum_to_the_full_estimate():
     from paper_2602_19697_gb300.sharding import estimate_variance_sharded, gpu_partial_fn
     c = case("sphere32_small")

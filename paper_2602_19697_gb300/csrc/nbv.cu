@@ -225,11 +225,11 @@ __global__ void k_nbv_sum(const double* __restrict__ part, int nblk, int V, doub
 }  // namespace
 
 // the candidates' predicted observations dd [V][N] (zeroed first)
-static void nbv_observations(bf_ctx* ctx, const bf_band* b, const float* mu, const float* cand, int V, const Intr& K,
-                             float* dd) {
+static bf_status nbv_observations(bf_ctx* ctx, const bf_band* b, const float* mu, const float* cand, int V,
+                                  const Intr& K, float* dd) {
   cudaStream_t st_ = ctx->stream;
   const int64_t N = b->N;
-  cudaMemsetAsync(dd, 0, (size_t)V * N * 4, st_);
+  BF_CK(cudaMemsetAsync(dd, 0, (size_t)V * N * 4, st_));
   const bf_params& p = b->prm;
   float tau = (float)p.band_vox * b->grid.voxel;
   float s2x = (float)(p.sig_pose * p.sig_pose + p.sig_model * p.sig_model);
@@ -239,6 +239,8 @@ static void nbv_observations(bf_ctx* ctx, const bf_band* b, const float* mu, con
   k_nbv_obs<<<(unsigned)g, 256, 0, st_>>>(band_view(b), mu, cand, V, K, tau, dda_max_steps(p.band_vox),
                                          (float)p.sig_a, (float)p.sig_b, s2x, dd, nullptr);
   count_launch();
+  BF_CK(cudaGetLastError());
+  return BF_OK;
 }
 
 // U [V] from the device copy dU: argmax and the copy to the caller's buffer
@@ -276,7 +278,7 @@ bf_status nbv_exact_impl(bf_ctx* ctx, bf_band* b, const float* mu, const float* 
   double* dU = part + (size_t)V * nblk;
   int tot = 0;
   if (N > 0) {
-    nbv_observations(ctx, b, mu, cand, V, K, dd);
+    BF_TRY(nbv_observations(ctx, b, mu, cand, V, K, dd));
     int it = 0;
     BF_TRY(variance_impl(ctx, b, 0, Kp, 1.0 / Kp, seed, tol, max_iter, R, 0u, s0, &it));
     tot += it;

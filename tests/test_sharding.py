@@ -63,3 +63,48 @@ def test_sharded_estimate_equals_single_process(tmp_path):
     for r in range(world):
         s = np.load(tmp_path / f"s{r}.npy")
         np.testing.assert_allclose(s, ref, rtol=1e-12, atol=1e-15)
+
+
+def _faulty_worker(rank, world, port, out_dir):
+    import datetime
+    import torch.distributed as dist
+    from paper_2602_19697_gb300.sharding import estimate_variance_sharded
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
+
+    def partial(k0, k1):
+        if rank == 1:
+            raise RuntimeError("probe solve failed on this rank")
+        return torch.ones(4, dtype=torch.float64)
+
+    try:
+        estimate_variance_sharded(partial, 8, rank, world)
+        result = "ok"
+    except Exception as e:  # the failing rank's own error, or the collective's on the others
+        result = type(e).__name__
+    with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+        f.write(result)
+    if rank == 1:
+        os._exit(3)  # the failed rank leaves without joining the all-reduce
+    os._exit(0)
+
+
+def test_a_failed_rank_is_reported_to_the_others_not_waited_for(tmp_path):
+    """Host-injected fault: rank 1's probe solve raises and the rank exits; rank 0's all-reduce must end with an
+    error (peer gone, or the process group's timeout) instead of hanging."""
+    world = 2
+    port = 29500 + ((os.getpid() + 517) % 1000)
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_faulty_worker, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    alive = [p for p in procs if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank hung"
+    assert procs[1].exitcode == 3
+    assert (tmp_path / "r1.txt").read_text() == "RuntimeError"
+    r0 = (tmp_path / "r0.txt").read_text()
+    assert r0 != "ok", r0

@@ -19,7 +19,7 @@ import numpy as np
 
 
 def run(workload: str = "sphere64", Ks=(4, 8, 16, 32, 64), candidates: int = 16, exact: bool = False,
-        seed: int = 0, rel_tol: float = 1e-8):
+        seed: int = 0, rel_tol: float = 1e-8, n=None, frames=None):
     import torch
 
     import synth
@@ -29,7 +29,7 @@ def run(workload: str = "sphere64", Ks=(4, 8, 16, 32, 64), candidates: int = 16,
     ctx = bfsdf.Context(0)
     rows = []
     for anchored in (True, False):
-        w = synth.make_workload(workload)
+        w = synth.make_workload(workload, n=n, frames=frames)
         w.lam_b = 1.0 if anchored else 0.0
         depth, poses = torch.from_numpy(w.depth).cuda(), torch.from_numpy(w.poses).cuda()
         band = ctx.build_band_w(w, depth, poses)
@@ -41,7 +41,7 @@ def run(workload: str = "sphere64", Ks=(4, 8, 16, 32, 64), candidates: int = 16,
             s = torch.empty(band.N, device="cuda")
             vi = band.estimate_variance(s, K=K, seed=seed, rel_tol=rel_tol, raise_on_fail=False)
             U, best = band.score_views(mu, s, cand, w.cand_intr)
-            row = {"workload": workload, "anchored": anchored, "lambda_b": w.lam_b, "K": K, "N_band": band.N,
+            row = {"workload": workload, "n": w.n, "frames": w.T, "anchored": anchored, "lambda_b": w.lam_b, "K": K, "N_band": band.N,
                    "mean_iters": info.iters, "mean_status": info.status, "variance_status": vi.status,
                    "best": best, "U_best": float(U[best]),
                    "U_mean": float(np.mean(U)), "s_mean": float(s.mean().item())}
@@ -62,8 +62,10 @@ def main(argv=None) -> None:
     ap.add_argument("--candidates", type=int, default=16)
     ap.add_argument("--exact", action="store_true", help="also the re-solved utilities (V + 1 estimates per K)")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--n", type=int, default=None, help="grid size (the voxel size scales so the scene fits)")
+    ap.add_argument("--frames", type=int, default=None, help="number of input views (fewer: sparser coverage)")
     a = ap.parse_args(argv)
-    run(a.workload, a.K, a.candidates, a.exact, a.seed)
+    run(a.workload, a.K, a.candidates, a.exact, a.seed, n=a.n, frames=a.frames)
 
 
 if __name__ == "__main__":

@@ -353,6 +353,51 @@ def score_views_exact(band: Band, mu, qdiag, lam, cand_poses, cand_intr, band_vo
     return U, int(np.argmax(U))
 
 
+def block_pcg(band: Band, lam, qdiag, B, tol=1e-12, max_iter=20000, rank_tol=1e-10):
+    """Block PCG with the Jacobi preconditioner for Q X = B (B [N, R]): the R right-hand sides share one block
+    Krylov space (O'Leary's block CG) in its breakdown-free form, the direction block kept as an orthonormal basis
+    from a rank-revealing QR so that converged or dependent directions drop out.  Per iteration, with P the basis:
+        alpha = (P^T Q P)^-1 P^T R,  X += P alpha,  R -= (Q P) alpha,
+        Z = M^-1 R,  beta = -(P^T Q P)^-1 (Q P)^T Z,  P = orth(Z + P beta).
+    Stops when every column's residual 2-norm is <= tol |b_c|.  Returns (X, status, iterations), status 0 on
+    convergence, 1 at max_iter."""
+    import scipy.linalg
+    import scipy.sparse
+    indptr, indices, data = csr(band, lam, qdiag)
+    Q = scipy.sparse.csr_matrix((data, indices, indptr), shape=(band.N, band.N))
+    B = np.asarray(B, np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    Minv = 1.0 / np.asarray(qdiag, np.float64)
+    bn = np.linalg.norm(B, axis=0)
+
+    def orth(Y):
+        Qf, Rf, _ = scipy.linalg.qr(Y, mode="economic", pivoting=True)
+        d = np.abs(np.diag(Rf))
+        keep = d > rank_tol * (d[0] if d.size and d[0] > 0 else 1.0)
+        return Qf[:, :int(np.count_nonzero(keep))]
+
+    X = np.zeros_like(B)
+    R = B.copy()
+    if np.all(np.linalg.norm(R, axis=0) <= tol * bn):
+        return X, 0, 0
+    P = orth(Minv[:, None] * R)
+    for it in range(1, max_iter + 1):
+        QP = Q @ P
+        G = P.T @ QP
+        alpha = np.linalg.solve(G, P.T @ R)
+        X += P @ alpha
+        R -= QP @ alpha
+        if np.all(np.linalg.norm(R, axis=0) <= tol * bn):
+            return X, 0, it
+        Z = Minv[:, None] * R
+        beta = -np.linalg.solve(G, QP.T @ Z)
+        P = orth(Z + P @ beta)
+        if P.shape[1] == 0:
+            return X, 0 if np.all(np.linalg.norm(R, axis=0) <= tol * bn) else 1, it
+    return X, 1, max_iter
+
+
 def solve_all(w, threads=0, tol=1e-12, K=None):
     """Full oracle pipeline for a workload: band, d/h, Q, mu and (optionally) s."""
     b = build_band_w(w, threads)

@@ -1,0 +1,121 @@
+"""Trilinear observation rows (Sec. 3.5: the linear relation y_i ~ a_i^T x with
+up to 8 non-zeros per row for trilinear interpolation) and the posterior
+system they give (Sec. 3.6: Q = Q0 + A^T W A, h = A^T W y + b0).
+
+TEST INFRASTRUCTURE: the FP64 reference of the trilinear form of the
+observation model, which the CUDA path does not implement yet (its rows are
+voxel-binned, one non-zero each, so its Q stays 7-point).  Only tests may use
+this module.
+
+Readings (where Sec. 3.5 leaves the sample placement open):
+  * a valid pixel (depth D > 0 and finite) gives the ray r = R d_c / |d_c|,
+    d_c = ((u + 1/2 - cx)/fx, (v + 1/2 - cy)/fy, 1), from the camera centre
+    C, hitting p = C + D R d_c at the distance s_p = D |d_c| along the ray;
+  * samples sit on the ray at s_k = s_p + k h for the integers k with
+    |k| h <= tau (tau = b h, b the band half-width in voxels): 2b + 1 per ray;
+  * each sample q_k observes the projective SDF y_k = clamp(<n, q_k - p>,
+    -tau, tau)/h with n = -r, i.e. y_k = (s_p - s_k)/h = -k (voxel units);
+  * its row a_k holds the trilinear weights of q_k in the cell of the 8 voxel
+    centres around it; a sample is used when every corner with a non-zero
+    weight is a band voxel (a sample on a centre needs that centre only);
+  * precision w = h^2 / sigma^2 with sigma^2 = (sig_a + sig_b D^2)^2 +
+    sig_pose^2 + sig_model^2, as for the voxel-binned rows.
+The prior is the one of the CUDA path: lambda (deg_j x_j - sum of the band
+6-neighbours) + lambda_b on the diagonal of the band boundary, and lambda_b
+tsdf_j / h in h.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def samples(depth, poses, intr, h, band_vox, sig_a, sig_b, sig_pose=0.0, sig_model=0.0):
+    """Sample points q [M,3] (metres), observations y [M] (voxels) and precisions w [M] of all valid pixels."""
+    depth = np.asarray(depth, np.float64)
+    poses = np.asarray(poses, np.float64)
+    fx, fy, cx, cy, W, H = intr
+    b = int(np.floor(band_vox + 1e-9))
+    ks = np.arange(-b, b + 1, dtype=np.float64)
+    qs, ys, ws = [], [], []
+    vv, uu = np.mgrid[0:H, 0:W]
+    dc = np.stack([(uu + 0.5 - cx) / fx, (vv + 0.5 - cy) / fy, np.ones((H, W))], -1).reshape(-1, 3)
+    ndc = np.linalg.norm(dc, axis=1)
+    for t in range(depth.shape[0]):
+        Dp = depth[t].reshape(-1)
+        ok = np.isfinite(Dp) & (Dp > 0)
+        if not np.any(ok):
+            continue
+        Rm, C = poses[t][:, :3], poses[t][:, 3]
+        r = (dc[ok] @ Rm.T) / ndc[ok][:, None]
+        sp = Dp[ok] * ndc[ok]
+        s = sp[:, None] + ks[None, :] * h                       # [P, 2b+1]
+        q = C[None, None, :] + s[..., None] * r[:, None, :]
+        sig2 = (sig_a + sig_b * Dp[ok] ** 2) ** 2 + sig_pose ** 2 + sig_model ** 2
+        w = np.repeat((h * h / sig2)[:, None], ks.size, 1)
+        y = np.clip(sp[:, None] - s, -band_vox * h, band_vox * h) / h
+        qs.append(q.reshape(-1, 3))
+        ys.append(y.reshape(-1))
+        ws.append(w.reshape(-1))
+    if not qs:
+        return np.zeros((0, 3)), np.zeros(0), np.zeros(0)
+    return np.concatenate(qs), np.concatenate(ys), np.concatenate(ws)
+
+
+def compact_map(band) -> np.ndarray:
+    """Dense map linear grid index -> compact band index (-1 outside the band)."""
+    m = np.full(band.n ** 3, -1, np.int64)
+    m[np.asarray(band.lin, np.int64)] = np.arange(band.N)
+    return m
+
+
+def trilinear_rows(band, q, cmap=None):
+    """For points q [M,3]: (idx [M,8] compact indices of the cell corners, wts [M,8] trilinear weights, used [M]),
+    corner c = (c & 1, (c >> 1) & 1, (c >> 2) & 1) offsets from the cell's lowest centre; a row is used when every
+    corner with a non-zero weight is a band voxel (idx of a zero-weight corner outside the band is 0; unused rows
+    have idx and wts 0)."""
+    n, h = band.n, band.h
+    cmap = compact_map(band) if cmap is None else cmap
+    g = (np.asarray(q, np.float64) - np.asarray(band.origin, np.float64)) / h - 0.5
+    i0 = np.floor(g).astype(np.int64)
+    f = g - i0
+    idx = np.zeros((len(g), 8), np.int64)
+    wts = np.zeros((len(g), 8), np.float64)
+    used = np.ones(len(g), bool)
+    for c in range(8):
+        o = np.array([c & 1, (c >> 1) & 1, (c >> 2) & 1])
+        ii = i0 + o
+        wc = np.prod(np.where(o[None, :] == 1, f, 1.0 - f), axis=1)
+        inside = np.all((ii >= 0) & (ii < n), axis=1)
+        lin = np.where(inside, ii[:, 0] + n * (ii[:, 1] + n * ii[:, 2]), 0)
+        j = np.where(inside, cmap[lin], -1)
+        used &= (j >= 0) | (wc == 0.0)
+        idx[:, c] = np.maximum(j, 0)
+        wts[:, c] = wc
+    idx[~used] = 0
+    wts[~used] = 0.0
+    return idx, wts, used
+
+
+def system(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, sig_pose=0.0, sig_model=0.0):
+    """(Q scipy CSR [N,N], h [N], d [N] = A^T w, number of used samples): the posterior precision and information
+    vector with trilinear observation rows."""
+    import scipy.sparse
+
+    from . import csr
+    q, y, w = samples(depth, poses, intr, band.h, band_vox, sig_a, sig_b, sig_pose, sig_model)
+    idx, wts, used = trilinear_rows(band, q)
+    idx, wts, y, w = idx[used], wts[used], y[used], w[used]
+    N = band.N
+    # A^T W A: for every row, w a a^T over its 8 x 8 corner pairs
+    rows = np.repeat(idx, 8, axis=1).reshape(-1)
+    cols = np.tile(idx, (1, 8)).reshape(-1)
+    vals = (w[:, None, None] * wts[:, :, None] * wts[:, None, :]).reshape(-1)
+    AtWA = scipy.sparse.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+    d = np.bincount(idx.reshape(-1), weights=(w[:, None] * wts).reshape(-1), minlength=N)
+    hd = np.bincount(idx.reshape(-1), weights=(w[:, None] * wts * y[:, None]).reshape(-1), minlength=N)
+    bd = np.asarray(band.bdry, np.float64)
+    prior_diag = lam * np.asarray(band.deg, np.float64) + lam_b * bd
+    indptr, indices, data = csr(band, lam, prior_diag)
+    Q0 = scipy.sparse.csr_matrix((data, indices, indptr), shape=(N, N))
+    hvec = hd + lam_b * bd * np.asarray(band.tsdf, np.float64) / band.h
+    return (Q0 + AtWA).tocsr(), hvec, d, int(used.sum())

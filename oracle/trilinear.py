@@ -23,6 +23,17 @@ Readings (where Sec. 3.5 leaves the sample placement open):
 The prior is the one of the CUDA path: lambda (deg_j x_j - sum of the band
 6-neighbours) + lambda_b on the diagonal of the band boundary, and lambda_b
 tsdf_j / h in h.
+
+FP32 specification of the row decisions (`rows_fp32`), for a kernel that must
+choose the same cells and weights bit for bit: every operation an IEEE FP32
+operation rounded on its own (no fused multiply-add), in this order --
+  dx = (u + 0.5 - cx) / fx,  dy = (v + 0.5 - cy) / fy   [((u + 0.5) - cx) / fx]
+  nrm = sqrt((dx dx + dy dy) + 1)
+  r_i = ((R_i0 dx + R_i1 dy) + R_i2) / nrm
+  s = D nrm + k h,  q_i = C_i + s r_i
+  g_i = (q_i - o_i) / h - 0.5,  i0_i = floor(g_i),  f_i = g_i - i0_i
+  weight of corner c = (w_x w_y) w_z, w = f_i for an upper corner, 1 - f_i for a lower one
+and a corner counts when its FP32 weight is not 0.
 """
 from __future__ import annotations
 
@@ -119,3 +130,60 @@ def system(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, sig_pos
     Q0 = scipy.sparse.csr_matrix((data, indices, indptr), shape=(N, N))
     hvec = hd + lam_b * bd * np.asarray(band.tsdf, np.float64) / band.h
     return (Q0 + AtWA).tocsr(), hvec, d, int(used.sum())
+
+
+def rows_fp32(band, depth, poses, intr, band_vox, cmap=None):
+    """The samples' rows under the FP32 specification above: (idx [M,8], wts [M,8] float32, used [M], y [M]),
+    samples in the order of ``samples`` (frames, then pixels row by row, then k)."""
+    f32 = np.float32
+    fx, fy, cx, cy, W, H = (f32(intr[0]), f32(intr[1]), f32(intr[2]), f32(intr[3]), int(intr[4]), int(intr[5]))
+    h = f32(band.h)
+    org = np.asarray(band.origin, f32)
+    n = band.n
+    cmap = compact_map(band) if cmap is None else cmap
+    b = int(np.floor(band_vox + 1e-9))
+    ks = np.arange(-b, b + 1).astype(f32)
+    vv, uu = np.mgrid[0:H, 0:W]
+    dx = ((uu.astype(f32) + f32(0.5)) - cx) / fx
+    dy = ((vv.astype(f32) + f32(0.5)) - cy) / fy
+    nrm = np.sqrt((dx * dx + dy * dy) + f32(1.0))
+    idxs, wtss, useds, ys = [], [], [], []
+    depth = np.asarray(depth, f32)
+    poses = np.asarray(poses, f32)
+    for t in range(depth.shape[0]):
+        Dp = depth[t]
+        ok = np.isfinite(Dp) & (Dp > 0)
+        if not np.any(ok):
+            continue
+        Rm, C = poses[t][:, :3], poses[t][:, 3]
+        r = [((Rm[i, 0] * dx[ok] + Rm[i, 1] * dy[ok]) + Rm[i, 2]) / nrm[ok] for i in range(3)]
+        sp = Dp[ok] * nrm[ok]
+        s = sp[:, None] + ks[None, :] * h
+        g = np.stack([(((C[i] + s * r[i][:, None]) - org[i]) / h) - f32(0.5) for i in range(3)], -1).reshape(-1, 3)
+        i0 = np.floor(g)
+        fr = g - i0
+        i0 = i0.astype(np.int64)
+        M = len(g)
+        idx = np.zeros((M, 8), np.int64)
+        wts = np.zeros((M, 8), f32)
+        used = np.ones(M, bool)
+        for c in range(8):
+            o = (c & 1, (c >> 1) & 1, (c >> 2) & 1)
+            wv = [fr[:, i] if o[i] else f32(1.0) - fr[:, i] for i in range(3)]
+            wc = (wv[0] * wv[1]) * wv[2]
+            ii = i0 + np.array(o)
+            inside = np.all((ii >= 0) & (ii < n), axis=1)
+            lin = np.where(inside, ii[:, 0] + n * (ii[:, 1] + n * ii[:, 2]), 0)
+            j = np.where(inside, cmap[lin], -1)
+            used &= (j >= 0) | (wc == 0)
+            idx[:, c] = np.maximum(j, 0)
+            wts[:, c] = wc
+        idx[~used] = 0
+        wts[~used] = 0
+        idxs.append(idx)
+        wtss.append(wts)
+        useds.append(used)
+        ys.append(np.repeat(-ks[None, :], len(sp), 0).reshape(-1).astype(np.float64))
+    if not idxs:
+        return np.zeros((0, 8), np.int64), np.zeros((0, 8), f32), np.zeros(0, bool), np.zeros(0)
+    return np.concatenate(idxs), np.concatenate(wtss), np.concatenate(useds), np.concatenate(ys)

@@ -116,3 +116,25 @@ def test_normal_incidence_mean_is_the_radial_sdf():
         assert e.mean() <= 0.03 and e.max() <= 0.15, (lam, e.mean(), e.max())
         errs.append(e.max())
     assert errs[1] <= errs[0]  # less smoothing, closer to the observed field
+
+
+def test_fp32_rows_follow_the_fp64_definition(sphere):
+    """The FP32-specified rows choose the FP64 definition's cell except for samples within FP32 rounding of a cell
+    face, and their weights agree to FP32 precision; the same input gives the same bits."""
+    w, b = sphere
+    q, y, wv = trilinear.samples(w.depth, w.poses, w.intr, b.h, w.band_vox, w.sig_a, w.sig_b)
+    idx, wts, used = trilinear.trilinear_rows(b, q)
+    idx32, wts32, used32, y32 = trilinear.rows_fp32(b, w.depth, w.poses, w.intr, w.band_vox)
+    assert len(idx32) == len(q)
+    np.testing.assert_allclose(y32, y, rtol=0, atol=1e-12)
+    g = (q - np.asarray(b.origin)) / b.h - 0.5
+    near_face = np.any(np.abs(g - np.round(g)) < 1e-4, axis=1)
+    same = ~near_face
+    assert same.mean() > 0.99
+    np.testing.assert_array_equal(used32[same], used[same])
+    both = same & used
+    np.testing.assert_array_equal(idx32[both], idx[both])
+    np.testing.assert_allclose(wts32[both], wts[both], rtol=0, atol=2e-5)
+    again = trilinear.rows_fp32(b, w.depth, w.poses, w.intr, w.band_vox)
+    np.testing.assert_array_equal(again[0], idx32)
+    np.testing.assert_array_equal(again[1], wts32)

@@ -353,18 +353,23 @@ def score_views_exact(band: Band, mu, qdiag, lam, cand_poses, cand_intr, band_vo
     return U, int(np.argmax(U))
 
 
-def block_pcg(band: Band, lam, qdiag, B, tol=1e-12, max_iter=20000, rank_tol=1e-10):
+def block_pcg(band: Band, lam, qdiag, B, tol=1e-12, max_iter=20000, rank_tol=1e-10, Q=None):
     """Block PCG with the Jacobi preconditioner for Q X = B (B [N, R]): the R right-hand sides share one block
     Krylov space (O'Leary's block CG) in its breakdown-free form, the direction block kept as an orthonormal basis
     from a rank-revealing QR so that converged or dependent directions drop out.  Per iteration, with P the basis:
         alpha = (P^T Q P)^-1 P^T R,  X += P alpha,  R -= (Q P) alpha,
         Z = M^-1 R,  beta = -(P^T Q P)^-1 (Q P)^T Z,  P = orth(Z + P beta).
-    Stops when every column's residual 2-norm is <= tol |b_c|.  Returns (X, status, iterations), status 0 on
-    convergence, 1 at max_iter."""
+    Stops when every column's residual 2-norm is <= tol |b_c|.  Q (a scipy sparse matrix) replaces the 7-point
+    precision built from lam and qdiag when given (its diagonal is then the preconditioner).  Returns (X, status,
+    iterations), status 0 on convergence, 1 at max_iter."""
     import scipy.linalg
     import scipy.sparse
-    indptr, indices, data = csr(band, lam, qdiag)
-    Q = scipy.sparse.csr_matrix((data, indices, indptr), shape=(band.N, band.N))
+    if Q is None:
+        indptr, indices, data = csr(band, lam, qdiag)
+        Q = scipy.sparse.csr_matrix((data, indices, indptr), shape=(band.N, band.N))
+    else:
+        Q = scipy.sparse.csr_matrix(Q)
+        qdiag = Q.diagonal()
     B = np.asarray(B, np.float64)
     if B.ndim == 1:
         B = B[:, None]

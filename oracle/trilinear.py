@@ -187,3 +187,19 @@ def rows_fp32(band, depth, poses, intr, band_vox, cmap=None):
     if not idxs:
         return np.zeros((0, 8), np.int64), np.zeros((0, 8), f32), np.zeros(0, bool), np.zeros(0)
     return np.concatenate(idxs), np.concatenate(wtss), np.concatenate(useds), np.concatenate(ys)
+
+
+def posterior(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, K, seed, tol=1e-12, sig_pose=0.0,
+              sig_model=0.0):
+    """(mu [N], s [N]) under trilinear rows: the MAP mean Q mu = h (sparse direct solve) and the K-probe estimate
+    s = (1/K) sum_k z_k (.) Q^-1 z_k with the probes of ``oracle.probe`` (block PCG over the K columns)."""
+    import scipy.sparse.linalg
+
+    from . import block_pcg, probe
+    Q, hv, _, _ = system(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, sig_pose, sig_model)
+    mu = scipy.sparse.linalg.spsolve(Q.tocsc(), hv)
+    Z = np.stack([probe(seed, k, band.lin) for k in range(K)], 1)
+    X, st, _ = block_pcg(band, lam, None, Z, tol=tol, Q=Q)
+    if st != 0:
+        raise RuntimeError("block PCG did not converge")
+    return mu, np.mean(Z * X, axis=1)

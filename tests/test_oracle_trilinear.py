@@ -138,3 +138,21 @@ def test_fp32_rows_follow_the_fp64_definition(sphere):
     again = trilinear.rows_fp32(b, w.depth, w.poses, w.intr, w.band_vox)
     np.testing.assert_array_equal(again[0], idx32)
     np.testing.assert_array_equal(again[1], wts32)
+
+
+def test_posterior_under_trilinear_rows_matches_dense_algebra():
+    """Mean and probe estimate of the 27-point system against a dense solve of the same system and probes."""
+    w = synth.make_workload("sphere64", n=16, image_scale=0.25, frames=8, noise=False)
+    b = oracle.build_band_w(w)
+    assert b.N <= 3000
+    K, seed = 6, 7
+    mu, s = trilinear.posterior(b, w.depth, w.poses, w.intr, w.band_vox, w.sig_a, w.sig_b, w.lam, w.lam_b, K, seed)
+    Q, hv, _, _ = trilinear.system(b, w.depth, w.poses, w.intr, w.band_vox, w.sig_a, w.sig_b, w.lam, w.lam_b)
+    Qd = Q.toarray()
+    np.testing.assert_allclose(mu, np.linalg.solve(Qd, hv), rtol=0, atol=1e-9 * np.abs(mu).max())
+    Z = np.stack([oracle.probe(seed, k, b.lin) for k in range(K)], 1)
+    ref = np.mean(Z * np.linalg.solve(Qd, Z), axis=1)
+    np.testing.assert_allclose(s, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    # and the probe-averaged value bounds: (Q^-1)_ii >= 1/Q_ii holds for the exact diagonal
+    Qi = np.linalg.inv(Qd)
+    assert np.all(np.diag(Qi) >= 1.0 / np.diag(Qd) * (1 - 1e-12))

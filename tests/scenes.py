@@ -34,3 +34,20 @@ def frontal_plane(n=32, h=0.015, z0_off=0.37, band_vox=3.0, trunc_vox=5.0, W=48,
     depth = synth.render(sc, P, W, W, f, f, W / 2, W / 2)
     return dict(n=n, h=h, Z0=Z0, org=org, poses=P.astype(np.float32), intr=intr, depth=depth,
                 band_vox=band_vox, trunc_vox=trunc_vox)
+
+
+def exterior_sphere(n=64, h=0.015, R=0.3, views=400, W=96, f=700.0, dist=1.0, band_vox=4.0, trunc_vox=6.0):
+    """A sphere of radius R at the origin seen, without noise, by `views`
+    cameras on a Fibonacci sphere of radius `dist` looking at its centre, with
+    a narrow field of view: a ray at angle phi off the optical axis meets the
+    sphere at incidence theta with sin(theta) = dist sin(phi) / R (law of
+    sines), so every ray meets the surface within theta_max of its normal."""
+    sc = synth.sphere_scene(R)
+    P = np.stack([synth.look_at(dist * v) for v in synth.fibonacci_sphere(views)])
+    intr = (f, f, W / 2, W / 2, W, W)
+    depth = synth.render(sc, P, W, W, f, f, W / 2, W / 2)
+    phi = np.arctan(np.hypot(W / 2, W / 2) / f)
+    theta_max = float(np.arcsin(dist * np.sin(phi) / R))
+    org = (-n * h / 2,) * 3
+    return dict(n=n, h=h, R=R, org=org, poses=P.astype(np.float32), intr=intr, depth=depth,
+                band_vox=band_vox, trunc_vox=trunc_vox, theta_max=theta_max)

@@ -31,6 +31,10 @@
  *    (bf_build_band, bf_extract_surface, bf_score_views and the iteration
  *    counts of the solvers).  The caller owns every array it passes; the
  *    library owns the context, the band and their workspaces.
+ *  - Devices: every call that takes a context first makes the context's
+ *    device the calling thread's current device (and leaves it current), so
+ *    one thread may drive contexts on several GPUs; bf_band_free and
+ *    bf_net_destroy switch to the device that holds the object.
  *  - Errors: every call returns a bf_status; BF_OK is 0.  The text of the
  *    last error of a context is available from bf_last_error.  A call that
  *    fails leaves its outputs unspecified but the context usable, except
@@ -170,7 +174,8 @@ bf_status bf_spmm(bf_ctx* ctx, bf_band* band, const float* X, int R, float* Y);
 /* MAP mean: solve Q mu = h by Jacobi-preconditioned CG (Sec. 3.6, MAP
  * equation; Algorithm 1 step 5).  Stops when ||r||_2 <= rel_tol ||h||_2 on
  * the recursive residual, then recomputes the true residual in FP64 and
- * restarts from the current iterate (at most 3 times) if it misses.
+ * restarts from the current iterate (at most 64 refinement passes) if it
+ * misses.
  *   mu [N] float (voxels); iters / rel_res (host, may be NULL) receive the
  *   iteration count and the final true relative residual.
  * Returns BF_NOT_CONVERGED after max_iter iterations (mu = last iterate),
@@ -194,14 +199,17 @@ bf_status bf_solve_mean(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter
 bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* band, int K, uint64_t seed, double rel_tol, int max_iter,
                                int rhs_block, unsigned flags, float* s, int* total_iters);
 
-/* Partial probe sum for sharding the estimator across devices or calls
- * (Sec. 3.7, diag equation): s_sum = sum_{k_begin <= k < k_end} z_k (.)
- * Q^-1 z_k with the probes of bf_estimate_variance (probe k is a function of
- * (seed, k, voxel) only), so disjoint ranges summed and divided by K give
- * bf_estimate_variance's s.  Arguments and errors as bf_estimate_variance. */
-bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* band, int k_begin, int k_end, uint64_t seed,
-                                     double rel_tol, int max_iter, int rhs_block, unsigned flags, float* s_sum,
-                                     int* total_iters);
+/* Scaled partial probe sum for sharding the estimator across devices or
+ * calls (Sec. 3.7, diag equation): s_part = scale * sum_{k_begin <= k < k_end}
+ * z_k (.) Q^-1 z_k with the probes of bf_estimate_variance (probe k is a
+ * function of (seed, k, voxel) only).  With scale = 1/K, the parts of
+ * disjoint ranges covering 0 .. K-1 add up to bf_estimate_variance's s (one
+ * sum across ranks, no division after it); scale = 1 gives the plain sum.
+ * scale must be finite and > 0 (else BF_EINVAL); other arguments and errors
+ * as bf_estimate_variance. */
+bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* band, int k_begin, int k_end, double scale,
+                                     uint64_t seed, double rel_tol, int max_iter, int rhs_block, unsigned flags,
+                                     float* s_part, int* total_iters);
 
 /* Marching cubes on mu (Sec. 3.8; Algorithm 1 step 7): every cube of 8 band
  * voxels, inside = mu < 0; per cube, polygons traced face by face
@@ -268,9 +276,11 @@ bf_status bf_autotune_rhs_block(bf_ctx* ctx, bf_band* band, int K, int force, in
  * the iterations.
  *   Limits: band of at most 262,144 voxels (else BF_EINVAL); mu [N] must be
  *   DEVICE memory (else BF_EINVAL); x0 = 0.  Errors are reported through the
- *   status only (bf_last_error is not updated).
- *   The first call on a device looks up the array's device address; make it
- *   before any stream capture.  All calls share the array: calls whose GPU
+ *   status only (bf_last_error is updated only when the switch to the
+ *   context's device fails).  At most 64 refinement passes, as in
+ *   bf_solve_mean.
+ *   The first call on a device looks up the array's device address (with
+ *   the context's device current); make it before any stream capture.  All calls share the array: calls whose GPU
  *   work overlaps (other streams or threads) race and must be serialised by
  *   the caller. */
 bf_status bf_solve_mean_static(bf_ctx* ctx, bf_band* band, double rel_tol, int max_iter, float* mu, int* iters,

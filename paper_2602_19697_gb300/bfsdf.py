@@ -107,7 +107,7 @@ def load_library(path: str = LIB_PATH):
         "bf_score_views_exact": (i, [vp, vp, vp, vp, i, ctypes.POINTER(Intrinsics), d, i, ctypes.c_uint64, d, i, i,
                                      vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "bf_solve_mean_static": (i, [vp, vp, d, i, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
-        "bf_estimate_variance_range": (i, [vp, vp, i, i, ctypes.c_uint64, d, i, i, u, vp, ctypes.POINTER(i)]),
+        "bf_estimate_variance_range": (i, [vp, vp, i, i, d, ctypes.c_uint64, d, i, i, u, vp, ctypes.POINTER(i)]),
         "bf_bench_kernel": (i, [vp, vp, i, i, i, ctypes.POINTER(d)]),
         "bf_launch_count": (i, [ctypes.POINTER(i64)]),
         "bf_net_nparams": (i64, []),
@@ -310,11 +310,12 @@ class Band:
             self.ctx.check(st, "bf_estimate_variance")
         return SolveInfo(it.value, 0.0, st)
 
-    def estimate_variance_range(self, s_sum, k_begin, k_end, seed=0, rel_tol=1e-6, max_iter=20000, rhs_block=0):
-        """Partial probe sum over probes [k_begin, k_end) (bf_estimate_variance_range)."""
+    def estimate_variance_range(self, s_part, k_begin, k_end, seed=0, rel_tol=1e-6, max_iter=20000, rhs_block=0,
+                                scale=1.0):
+        """scale x the probe sum over probes [k_begin, k_end) (bf_estimate_variance_range)."""
         it = ctypes.c_int()
-        st = self.ctx.lib.bf_estimate_variance_range(self.ctx._p, self._p, int(k_begin), int(k_end), int(seed),
-                                                     rel_tol, max_iter, int(rhs_block), 0, _ptr(s_sum),
+        st = self.ctx.lib.bf_estimate_variance_range(self.ctx._p, self._p, int(k_begin), int(k_end), float(scale),
+                                                     int(seed), rel_tol, max_iter, int(rhs_block), 0, _ptr(s_part),
                                                      ctypes.byref(it))
         self.ctx.check(st, "bf_estimate_variance_range")
         return SolveInfo(it.value, 0.0, st)

@@ -2,6 +2,7 @@
 // staging, context and workspace management.  The computation lives in the
 // other translation units.
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -138,6 +139,7 @@ bf_status bf_create(int device, void* stream, bf_ctx** out) {
 
 void bf_destroy(bf_ctx* ctx) {
   if (!ctx) return;
+  enter_device(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (auto& w : ctx->ws)
     if (w.p) cudaFree(w.p);
@@ -161,6 +163,7 @@ bf_status bf_set_stream(bf_ctx* ctx, void* stream) {
 
 bf_status bf_build_band(bf_ctx* ctx, const float* depth, int T, const float* poses, const bf_intrinsics* K,
                         const bf_grid* grid, const bf_params* prm, bf_band** out) {
+  BF_ENTER(ctx);
   if (!ctx || !out) return BF_EINVAL;
   *out = nullptr;
   if (!depth || !poses || !grid || !prm || T < 1 || !valid_intr(K))
@@ -170,7 +173,6 @@ bf_status bf_build_band(bf_ctx* ctx, const float* depth, int T, const float* pos
   if (!(prm->band_vox > 0.0) || !(prm->trunc_vox > prm->band_vox) || prm->trunc_vox > 256.0 ||
       !(prm->lambda >= 0.0) || !(prm->lambda_b >= 0.0))
     return bf_fail(ctx, BF_EINVAL, "bf_build_band: need 0 < band_vox < trunc_vox <= 256, lambda, lambda_b >= 0");
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return bf_fail(ctx, BF_ECUDA, "cudaSetDevice");
   const float *d_depth, *d_poses;
   size_t npix = (size_t)T * K->H * K->W;
   BF_TRY(stage_in(ctx, depth, npix, WS_STAGE0, &d_depth));
@@ -180,6 +182,7 @@ bf_status bf_build_band(bf_ctx* ctx, const float* depth, int T, const float* pos
 
 void bf_band_free(bf_band* b) {
   if (!b) return;
+  enter_device(b->device);
   cudaStreamSynchronize(b->stream);
   void* ptrs[] = {b->dir, b->bcoord, b->meta, b->off, b->nbr, b->lin, b->tsdf, b->wcount, b->info,
                   b->d, b->hd, b->qd, b->rhs, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot, b->dfx, b->hfx};
@@ -198,6 +201,7 @@ bf_status bf_band_info(const bf_band* b, int64_t* n_vox, int32_t* n_bricks, int6
 
 bf_status bf_export_band(bf_ctx* ctx, const bf_band* b, int64_t* lin, float* tsdf, int32_t* wcount, uint8_t* bdry,
                          int32_t* brick_dir, uint64_t* mask) {
+  BF_ENTER(ctx);
   if (!ctx || !b) return BF_EINVAL;
   cudaStream_t s = ctx->stream;
   const int64_t N = b->N;
@@ -240,6 +244,7 @@ bf_status bf_export_band(bf_ctx* ctx, const bf_band* b, int64_t* lin, float* tsd
 
 bf_status bf_integrate_depth_ex(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses,
                                 const bf_intrinsics* K, unsigned flags) {
+  BF_ENTER(ctx);
   if (!ctx || !b) return BF_EINVAL;
   if (!depth || !poses || T < 1 || !valid_intr(K))
     return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth: null pointer, T < 1 or bad intrinsics");
@@ -256,6 +261,7 @@ bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* b, const float* depth, int T,
 }
 
 bf_status bf_reset_observations(bf_ctx* ctx, bf_band* b) {
+  BF_ENTER(ctx);
   if (!ctx || !b) return BF_EINVAL;
   b->obs_mode = 0;
   if (b->dfx) {
@@ -271,6 +277,7 @@ bf_status bf_reset_observations(bf_ctx* ctx, bf_band* b) {
 }
 
 bf_status bf_export_system(bf_ctx* ctx, const bf_band* b, float* d, float* hdata, float* qdiag, float* rhs) {
+  BF_ENTER(ctx);
   if (!ctx || !b) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_export_system: call bf_integrate_depth first");
   const float* src[4] = {b->d, b->hd, b->qd, b->rhs};
@@ -287,6 +294,7 @@ bf_status bf_export_system(bf_ctx* ctx, const bf_band* b, float* d, float* hdata
 }
 
 bf_status bf_export_observations_f64(bf_ctx* ctx, const bf_band* b, double* d, double* hdata) {
+  BF_ENTER(ctx);
   if (!ctx || !b) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_export_observations_f64: call bf_integrate_depth first");
   if (!b->N || (!d && !hdata)) return BF_OK;
@@ -301,6 +309,7 @@ bf_status bf_export_observations_f64(bf_ctx* ctx, const bf_band* b, double* d, d
 }
 
 bf_status bf_spmv(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !x || !y) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_spmv: call bf_integrate_depth first");
   const float* dx;
@@ -313,6 +322,7 @@ bf_status bf_spmv(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
 }
 
 bf_status bf_spmm(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !X || !Y) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_spmm: call bf_integrate_depth first");
   if (R != 8 && R != 16 && R != 32) return bf_fail(ctx, BF_EINVAL, "bf_spmm: R must be 8, 16 or 32");
@@ -328,6 +338,7 @@ bf_status bf_spmm(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y) {
 
 bf_status bf_solve_mean(bf_ctx* ctx, bf_band* b, double rel_tol, int max_iter, unsigned flags, float* mu,
                         int* iters, double* rel_res) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !mu) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_solve_mean: call bf_integrate_depth first");
   if (!(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
@@ -347,6 +358,7 @@ bf_status bf_solve_mean(bf_ctx* ctx, bf_band* b, double rel_tol, int max_iter, u
 
 bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, double rel_tol, int max_iter,
                                int rhs_block, unsigned flags, float* s, int* total_iters) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !s) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_estimate_variance: call bf_integrate_depth first");
   if (K < 1 || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
@@ -364,18 +376,23 @@ bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, do
   return st;
 }
 
-bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* b, int k_begin, int k_end, uint64_t seed, double rel_tol,
-                                     int max_iter, int rhs_block, unsigned flags, float* s_sum, int* total_iters) {
+bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* b, int k_begin, int k_end, double scale, uint64_t seed,
+                                     double rel_tol, int max_iter, int rhs_block, unsigned flags, float* s_sum,
+                                     int* total_iters) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !s_sum) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_estimate_variance_range: call bf_integrate_depth first");
   if (k_begin < 0 || k_end <= k_begin || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: need 0 <= k_begin < k_end, 0 < rel_tol < 1");
+  if (!(scale > 0.0) || !std::isfinite(scale))
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: scale must be finite and > 0");
   if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: rhs_block must be 0, 1, 8, 16 or 32");
   float* ds;
   bool host;
   BF_TRY(stage_out(ctx, s_sum, b->N, WS_OUT1, &ds, &host));
-  bf_status st = variance_impl(ctx, b, k_begin, k_end, 1.0, seed, rel_tol, max_iter, rhs_block, flags, ds, total_iters);
+  bf_status st = variance_impl(ctx, b, k_begin, k_end, scale, seed, rel_tol, max_iter, rhs_block, flags, ds,
+                               total_iters);
   if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
     bf_status c = copy_out(ctx, s_sum, (const float*)ds, b->N, host);
     if (c != BF_OK) return c;
@@ -384,6 +401,7 @@ bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* b, int k_begin, int k
 }
 
 bf_status bf_extract_surface(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !mu || !nv || !nt) return BF_EINVAL;
   const float* dmu;
   BF_TRY(stage_in(ctx, mu, b->N, WS_STAGE2, &dmu));
@@ -391,6 +409,7 @@ bf_status bf_extract_surface(bf_ctx* ctx, const bf_band* b, const float* mu, int
 }
 
 bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris) {
+  BF_ENTER(ctx);
   if (!ctx) return BF_EINVAL;
   if (verts && ctx->mesh_nv) {
     cudaMemcpyKind k = is_device_ptr(verts) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -406,6 +425,7 @@ bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris) {
 
 bf_status bf_score_views(bf_ctx* ctx, const bf_band* b, const float* mu, const float* s, const float* cand, int V,
                          const bf_intrinsics* K, double eps, double* U, int* best) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !mu || !s || !cand || !U || V < 1 || !valid_intr(K) || !(eps >= 0.0))
     return bf_fail(ctx, BF_EINVAL, "bf_score_views: null pointer, V < 1, eps < 0 or bad intrinsics");
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_score_views: call bf_integrate_depth first");
@@ -419,6 +439,7 @@ bf_status bf_score_views(bf_ctx* ctx, const bf_band* b, const float* mu, const f
 bf_status bf_score_views_exact(bf_ctx* ctx, bf_band* b, const float* mu, const float* cand, int V,
                                const bf_intrinsics* K, double eps, int K_probes, uint64_t seed, double rel_tol,
                                int max_iter, int rhs_block, double* U, int* best, int* total_iters) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !mu || !cand || !U || V < 1 || !valid_intr(K) || !(eps >= 0.0) || K_probes < 1 ||
       !(rel_tol > 0.0) || max_iter < 1)
     return bf_fail(ctx, BF_EINVAL, "bf_score_views_exact: null pointer, V < 1, K < 1, eps < 0, rel_tol <= 0, "
@@ -434,6 +455,7 @@ bf_status bf_score_views_exact(bf_ctx* ctx, bf_band* b, const float* mu, const f
 }
 
 bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms_per_launch) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !ms_per_launch || reps < 1 || reps > 100000) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_bench_kernel: call bf_integrate_depth first");
   if (b->N == 0) return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: empty band");

@@ -283,6 +283,7 @@ bf_status band_build(bf_ctx* ctx, const float* depth, int T, const float* poses,
   b->nb = nb;
   b->ncand = ncand;
   b->stream = s;
+  b->device = ctx->device;
   auto fail = [&](bf_status e) {
     bf_band_free(b);
     return e;

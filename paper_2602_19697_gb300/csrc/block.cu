@@ -1188,7 +1188,7 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
     BF_CK(cudaGetLastError());
     bool done = false;
     int nouter = 0;  // residual passes run (the last one leaves the block's probe sums in hsum, hsq)
-    for (int outer = 0; outer < 64; ++outer) {
+    for (int outer = 0; outer < REFINE_MAX_PASSES; ++outer) {
       // correction solve (its first kernel ends the loop at once if the state is already final), then the
       // residual pass and the next start; the host looks at the state only after each residual pass
       BF_CK(cudaGraphLaunch(g->exec, s));

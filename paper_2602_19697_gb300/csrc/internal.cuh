@@ -23,6 +23,24 @@
     if (s__ != BF_OK) return s__;        \
   } while (0)
 
+// Every entry point that takes a context runs on the context's device: the
+// calling thread's current device is switched to it (and left there).
+inline cudaError_t enter_device(int device) {
+  int cur = -1;
+  if (cudaGetDevice(&cur) == cudaSuccess && cur == device) return cudaSuccess;
+  return cudaSetDevice(device);
+}
+#define BF_ENTER(ctx)                                                                       \
+  do {                                                                                      \
+    if (!(ctx)) return BF_EINVAL;                                                           \
+    cudaError_t e__ = enter_device((ctx)->device);                                          \
+    if (e__ != cudaSuccess) return bf_fail(ctx, BF_ECUDA, "cudaSetDevice", cudaGetErrorString(e__)); \
+  } while (0)
+
+// Refinement passes (true-residual recomputation and restart) of the mean
+// solvers before they report BF_NOT_CONVERGED.
+constexpr int REFINE_MAX_PASSES = 64;
+
 struct Workspace {
   void* p = nullptr;
   size_t cap = 0;
@@ -74,6 +92,7 @@ struct bf_band {
   int64_t N = 0;
   int64_t ncand = 0;
   cudaStream_t stream = nullptr;  // stream the arrays were allocated on
+  int device = 0;                 // device that holds them
   // directory and per-brick data
   int32_t* dir = nullptr;     // [nb^3] rank or -1
   int32_t* bcoord = nullptr;  // [NB][4] (bi, bj, bk, 0)

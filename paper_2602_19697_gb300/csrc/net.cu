@@ -759,6 +759,7 @@ struct bf_net {
   double* h_loss = nullptr;
   int* err = nullptr;  // set by a tensor-core kernel whose MMAs did not complete in time
   bool attr = false;
+  int device = 0;      // device that holds the parameters and activations
 };
 
 static int64_t nparams_impl() {
@@ -932,8 +933,10 @@ extern "C" {
 int64_t bf_net_nparams(void) { return nparams_impl(); }
 
 bf_status bf_net_create(bf_ctx* ctx, uint64_t seed, bf_net** out) {
+  BF_ENTER(ctx);
   if (!ctx || !out) return BF_EINVAL;
   bf_net* net = new bf_net();
+  net->device = ctx->device;
   net->P = nparams_impl();
   int64_t o = 0;
   for (int l = 0; l < 4; ++l) {
@@ -971,6 +974,7 @@ bf_status bf_net_create(bf_ctx* ctx, uint64_t seed, bf_net** out) {
 
 void bf_net_destroy(bf_net* net) {
   if (!net) return;
+  enter_device(net->device);
   cudaDeviceSynchronize();
   void* ptrs[] = {net->p, net->g, net->m, net->v, net->loss, net->err};
   for (void* q : ptrs)
@@ -989,6 +993,7 @@ void bf_net_destroy(bf_net* net) {
 }
 
 bf_status bf_net_get_params(bf_ctx* ctx, const bf_net* net, float* params) {
+  BF_ENTER(ctx);
   if (!ctx || !net || !params) return BF_EINVAL;
   BF_CK(cudaMemcpyAsync(params, net->p, net->P * 4, cudaMemcpyDefault, ctx->stream));
   BF_CK(cudaStreamSynchronize(ctx->stream));
@@ -996,6 +1001,7 @@ bf_status bf_net_get_params(bf_ctx* ctx, const bf_net* net, float* params) {
 }
 
 bf_status bf_net_set_params(bf_ctx* ctx, bf_net* net, const float* params) {
+  BF_ENTER(ctx);
   if (!ctx || !net || !params) return BF_EINVAL;
   BF_CK(cudaMemcpyAsync(net->p, params, net->P * 4, cudaMemcpyDefault, ctx->stream));
   BF_CK(cudaMemsetAsync(net->m, 0, net->P * 4, ctx->stream));
@@ -1007,6 +1013,7 @@ bf_status bf_net_set_params(bf_ctx* ctx, bf_net* net, const float* params) {
 }
 
 bf_status bf_net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, float* mu_hat, float* log_s_hat) {
+  BF_ENTER(ctx);
   if (!ctx || !net || !b || !mu_hat || !log_s_hat) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_net_forward: call bf_integrate_depth first");
   if (b->N == 0) return BF_OK;
@@ -1023,6 +1030,7 @@ bf_status bf_net_forward(bf_ctx* ctx, bf_net* net, const bf_band* b, float* mu_h
 
 bf_status bf_net_train_step(bf_ctx* ctx, bf_net* net, const bf_band* b, const float* mu_t, const float* s_t,
                             float lr, double* loss, float* grad_out) {
+  BF_ENTER(ctx);
   if (!ctx || !net || !b || !mu_t || !s_t) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_net_train_step: call bf_integrate_depth first");
   if (!(lr >= 0.0f) || !(lr < 1.0f)) return bf_fail(ctx, BF_EINVAL, "bf_net_train_step: need 0 <= lr < 1");
@@ -1055,6 +1063,7 @@ bf_status bf_net_train_step(bf_ctx* ctx, bf_net* net, const bf_band* b, const fl
 bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat, int K, int K_judge, uint64_t seed,
                                 double rel_tol, int max_iter, int rhs_block, unsigned flags, float* s,
                                 uint8_t* accepted, double* brick_stat, int* n_accepted, int* total_iters) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !log_s_hat || !s) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_surrogate_variance: call bf_integrate_depth first");
   if (K_judge < 2 || K <= K_judge || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
@@ -1125,6 +1134,7 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
 }
 
 bf_status bf_net_bench(bf_ctx* ctx, bf_net* net, const bf_band* b, int which, int reps, double* ms) {
+  BF_ENTER(ctx);
   if (!ctx || !net || !b || !ms || reps < 1 || which < 0 || which > 4) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_net_bench: call bf_integrate_depth first");
   *ms = 0.0;

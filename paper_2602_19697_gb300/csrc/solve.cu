@@ -736,7 +736,7 @@ static bf_status solve_t(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsi
   count_launch();
   BF_CK(cudaGetLastError());
   bool done = false;
-  for (int outer = 0; outer < 64; ++outer) {
+  for (int outer = 0; outer < REFINE_MAX_PASSES; ++outer) {
     BF_CK(cudaMemcpyAsync(g->h_st, g->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
     BF_CK(cudaStreamSynchronize(s));
     if (g->h_st->done) {
@@ -755,7 +755,11 @@ static bf_status solve_t(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsi
   k_cast_out<<<gsz(N), 256, 0, s>>>(N, h.x64, mu);
   count_launch();
   BF_CK(cudaGetLastError());
+  if (!done) {  // the last pass's residual check has not been read back yet
+    BF_CK(cudaMemcpyAsync(g->h_st, g->st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+  }
   BF_CK(cudaStreamSynchronize(s));
+  if (!done) done = g->h_st->done;
   const PcgState& st = *g->h_st;
   count_launch(st.nexec);
   if (iters) *iters = st.iter;

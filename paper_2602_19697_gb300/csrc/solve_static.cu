@@ -348,6 +348,7 @@ unsigned char* g_scratch_addr[64] = {nullptr};
 
 extern "C" bf_status bf_solve_mean_static(bf_ctx* ctx, bf_band* b, double rel_tol, int max_iter, float* mu,
                                           int* iters, double* rel_res) {
+  BF_ENTER(ctx);
   if (!ctx || !b || !mu) return BF_EINVAL;
   if (!b->integrated) return BF_ESTATE;
   if (!(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000) return BF_EINVAL;
@@ -381,7 +382,7 @@ extern "C" bf_status bf_solve_mean_static(bf_ctx* ctx, bf_band* b, double rel_to
   count_launch();
   SState* hs = (SState*)ctx->h_pinned;  // 64 pinned bytes owned by the context; the first 32 are read
   bool done = false;
-  for (int outer = 0; outer < 32 && !done; ++outer) {
+  for (int outer = 0; outer < REFINE_MAX_PASSES && !done; ++outer) {
     k_s_res<<<gB, SBT, 0, s>>>(base, bv, lam, b->qd, b->rhs);
     count_launch();
     if (cudaMemcpyAsync(hs, base + S_STATE, 32, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

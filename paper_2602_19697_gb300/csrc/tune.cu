@@ -133,6 +133,7 @@ bf_status autotune_rhs_block(bf_ctx* ctx, bf_band* b, int K, bool force, int* R_
 
 extern "C" bf_status bf_autotune_rhs_block(bf_ctx* ctx, bf_band* band, int K, int force, int* rhs_block,
                                            double* ms_per_iter) {
+  BF_ENTER(ctx);
   if (!ctx || !band || !rhs_block || K < 1) return BF_EINVAL;
   if (!band->integrated) return bf_fail(ctx, BF_ESTATE, "bf_autotune_rhs_block: call bf_integrate_depth first");
   if (band->N == 0) {

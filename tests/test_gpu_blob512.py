@@ -68,8 +68,8 @@ def test_blob_mean_meets_the_residual_at_1e6_and_the_oracle_at_1e8(blob):
 def test_blob_variance_on_a_probe_sample(blob):
     gb = blob["gb"]
     ssum = torch.empty(gb.N, device="cuda")
-    gb.estimate_variance_range(ssum, 0, KS, seed=SEED, rel_tol=1e-6, rhs_block=32)
-    s = ssum.cpu().numpy().astype(np.float64) / KS
+    gb.estimate_variance_range(ssum, 0, KS, seed=SEED, rel_tol=1e-6, rhs_block=32, scale=1.0 / KS)
+    s = ssum.cpu().numpy().astype(np.float64)
     rel = np.abs(s - blob["s"]) / np.maximum(np.abs(blob["s"]), 1.0 / blob["qd"])
     assert rel.max() <= 1e-3, rel.max()
 

@@ -288,7 +288,7 @@ def test_exact_view_utilities_match_oracle(name, R):
 
 
 def test_probe_ranges_sum_to_the_full_estimate():
-    from paper_2602_19697_gb300.sharding import estimate_variance_sharded, gpu_partial_fn
+    from paper_2602_19697_gb300.sharding import estimate_variance_sharded, gpu_part_fn
     c = case("sphere32_small")
     w = c["w"]
     gb, depth, poses = gpu_band(w)
@@ -296,11 +296,15 @@ def test_probe_ranges_sum_to_the_full_estimate():
     K = 20
     s = torch.empty(gb.N, device="cuda")
     gb.estimate_variance(s, K=K, seed=5, rel_tol=1e-8, rhs_block=8)
-    fn = gpu_partial_fn(gb, gb.N, seed=5, rel_tol=1e-8, rhs_block=8)
-    parts = fn(0, 7) + fn(7, 20)          # two "ranks"
-    np.testing.assert_allclose((parts / K).cpu().numpy(), s.cpu().numpy(), rtol=2e-5, atol=0)
+    fn = gpu_part_fn(gb, gb.N, K, seed=5, rel_tol=1e-8, rhs_block=8)
+    parts = fn(0, 7) + fn(7, 20)          # two "ranks", each part scaled by 1/K in the library
+    np.testing.assert_allclose(parts.cpu().numpy(), s.cpu().numpy(), rtol=2e-5, atol=0)
     one = estimate_variance_sharded(fn, K, 0, 1)   # one rank: no collective
     np.testing.assert_allclose(one.cpu().numpy(), s.cpu().numpy(), rtol=2e-5, atol=0)
+    # scale = 1 gives the plain sum
+    ssum = torch.empty(gb.N, device="cuda")
+    gb.estimate_variance_range(ssum, 0, K, seed=5, rel_tol=1e-8, rhs_block=8, scale=1.0)
+    np.testing.assert_allclose(ssum.cpu().numpy() / K, s.cpu().numpy(), rtol=2e-5, atol=0)
 
 
 def test_autotuner_choice_cache_and_library_default(tmp_path, monkeypatch):

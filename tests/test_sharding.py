@@ -42,7 +42,7 @@ def _worker(rank, world, port, K, seed, out_dir):
         if k1 <= k0:
             return torch.zeros(b.N, dtype=torch.float64)
         s, st, it, _ = oracle.hutchinson(b, w.lam, qd, k1 - k0, seed, tol=1e-12, k0=k0)
-        return torch.from_numpy(s * (k1 - k0))
+        return torch.from_numpy(s * ((k1 - k0) / K))     # this rank's part, scaled by 1/K
 
     s = estimate_variance_sharded(partial, K, rank, world)
     np.save(os.path.join(out_dir, f"s{rank}.npy"), s.numpy())
@@ -65,46 +65,60 @@ def test_sharded_estimate_equals_single_process(tmp_path):
         np.testing.assert_allclose(s, ref, rtol=1e-12, atol=1e-15)
 
 
-def _faulty_worker(rank, world, port, out_dir):
+def _faulty_worker(rank, world, port, out_dir, die):
     import datetime
     import torch.distributed as dist
     from paper_2602_19697_gb300.sharding import estimate_variance_sharded
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=20))
 
-    def partial(k0, k1):
+    def part(k0, k1):
         if rank == 1:
+            if die:
+                os._exit(3)  # the rank disappears before any collective
             raise RuntimeError("probe solve failed on this rank")
         return torch.ones(4, dtype=torch.float64)
 
     try:
-        estimate_variance_sharded(partial, 8, rank, world)
+        estimate_variance_sharded(part, 8, rank, world)
         result = "ok"
-    except Exception as e:  # the failing rank's own error, or the collective's on the others
+    except Exception as e:  # the failing rank's own error, or the error the others receive
         result = type(e).__name__
     with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
         f.write(result)
-    if rank == 1:
-        os._exit(3)  # the failed rank leaves without joining the all-reduce
-    os._exit(0)
+    os._exit(3 if rank == 1 else 0)
 
 
-def test_a_failed_rank_is_reported_to_the_others_not_waited_for(tmp_path):
-    """Host-injected fault: rank 1's probe solve raises and the rank exits; rank 0's all-reduce must end with an
-    error (peer gone, or the process group's timeout) instead of hanging."""
+def _run_faulty(tmp_path, die):
     world = 2
-    port = 29500 + ((os.getpid() + 517) % 1000)
+    port = 29500 + ((os.getpid() + (517 if die else 733)) % 1000)
     ctx = mp.get_context("spawn")
-    procs = [ctx.Process(target=_faulty_worker, args=(r, world, port, str(tmp_path))) for r in range(world)]
+    procs = [ctx.Process(target=_faulty_worker, args=(r, world, port, str(tmp_path), die)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
-        p.join(timeout=120)
+        p.join(timeout=60)
     alive = [p for p in procs if p.is_alive()]
     for p in alive:
         p.kill()
     assert not alive, "a rank hung"
     assert procs[1].exitcode == 3
+    return (tmp_path / "r0.txt").read_text()
+
+
+def test_a_failed_rank_is_named_to_the_others(tmp_path):
+    """Host-injected fault: rank 1's probe solve raises.  It reports the
+    failure in the status all-reduce and re-raises its own error; rank 0
+    raises ProbeShardError instead of summing a partial result."""
+    r0 = _run_faulty(tmp_path, die=False)
     assert (tmp_path / "r1.txt").read_text() == "RuntimeError"
-    r0 = (tmp_path / "r0.txt").read_text()
-    assert r0 != "ok", r0
+    assert r0 == "ProbeShardError", r0
+
+
+def test_a_vanished_rank_ends_the_others_collective_with_an_error(tmp_path):
+    """Host-injected fault: rank 1 exits before any collective.  Rank 0's
+    status all-reduce ends with the process group's error (the peer's
+    connection closed, or the 20 s group timeout) instead of hanging."""
+    r0 = _run_faulty(tmp_path, die=True)
+    assert r0 not in ("ok", "ProbeShardError"), r0
+    assert r0 in ("RuntimeError", "DistBackendError", "DistNetworkError"), r0

@@ -1,21 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the narrow-band GRF posterior solve on one node.
 
-One step = the whole hot path on one synthetic depth sequence, inputs already
-resident in device memory: build_band -> integrate_depth -> solve_mean ->
-estimate_variance -> extract_surface -> score_views.  The headline metric
-is the posterior solve time (solve_mean + estimate_variance, FP32 vectors
-with FP64 dots and refinement, rel_tol 1e-6, 64 probes), read from CUDA
-events on the library's stream.  Also reported: the full step time, the
-same metric end to end through the C ABI with pinned host buffers (H2D of
-the frames and D2H of mu and s inside the timed region), the roofline of
-the dominant kernel (event-timed by bf_bench_kernel), and the CPU oracle
-timed on a bounded sample of the same workload.
+Workload (default): the 200-frame object sequence -- a seeded spherical-
+harmonic blob in a 512^3 grid at 2 mm, band +-24 voxels (7.2 M band
+voxels), 200 depth frames 512x384 on a spiral orbit, 128 probes.
 
-Multi-GPU: one process per GPU (torchrun); every rank solves its own
-instance of the workload (noise seed = rank) with no collective on the data
-path (replicas: the box has one GPU per solve); value = max-over-ranks time /
-posteriors solved.
+One step = the whole hot path on that synthetic depth sequence, inputs
+already resident in device memory: build_band -> integrate_depth ->
+solve_mean -> estimate_variance -> extract_surface -> score_views.  The
+headline value is the time to posterior, solve_mean + estimate_variance
+(FP32 vectors, FP64 inner products and refinement), read from CUDA events
+on the library's stream: the probes to rel_tol 1e-6, the mean to 1e-8 (the
+tolerance at which it meets the 1e-3-voxel parity bar; its 1e-6 time is
+reported beside it).  Also reported: the full step time; the same metric end
+to end through the C ABI with pinned host buffers (H2D of the frames and D2H
+of mu and s inside the timed region); the roofline of the dominant kernel
+(the probe solver's iteration, event-timed by bf_bench_kernel) and of the
+single-RHS SpMV on the same band with L2 flushed; the posterior in its
+unbatched, block and learned-warm-start forms; and the CPU oracle timed on a
+bounded sample of the same workload.
+
+Multi-GPU (torchrun, one process per GPU): one posterior per job with its
+K probes split across the ranks (bf_estimate_variance_range with scale 1/K,
+then one NCCL all-reduce of s); the mean, the mesh and the view scores are
+computed on rank 0.  Strong scaling: value = max-over-ranks time per
+posterior.
 """
 from __future__ import annotations
 
@@ -33,6 +42,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "posterior solve s (mean+diag var) at 1e-6 rel residual; SpMV GB/s vs HBM peak"
 
+# DRAM bytes (read + write) per launch of the probe solver's iteration, from one ncu capture of that kernel on
+# the band it was taken on (dram__bytes_read.sum + dram__bytes_write.sum, mean of an x-writing and an x-holding
+# launch); keyed by (band voxels, block width); valid for the kernel as it was when captured.
+BLK_IT_TRAFFIC = {}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -40,17 +54,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="union256",
-                    help="union256 | sphere64 | blob512 | blob1024 (--kernel only: the blob512 object at 1 mm on a "
-                         "1024^3 grid, band +-48 voxels, 200 frames 1024x768; a band of about 58 M voxels)")
-    ap.add_argument("--K", type=int, default=64)
-    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--workload", default="blob512",
+                    help="blob512 | union256 | sphere64 | sphere64_k256 | blob1024 (--kernel only: the blob512 "
+                         "object at 1 mm on a 1024^3 grid, band +-48 voxels, 200 frames 1024x768; 61 M voxels)")
+    ap.add_argument("--K", type=int, default=None, help="probes (default: the workload's, 128 for blob512)")
+    ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the probe solves")
+    ap.add_argument("--mean-tol", type=float, default=1e-8,
+                    help="relative residual of the timed mean solve (1e-8: the 1e-3-voxel parity tolerance)")
     ap.add_argument("--rhs-block", type=int, default=0, help="probe block width (0 = the library's autotuner)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-object", action="store_true",
-                    help="skip the 512^3 object-sequence measurements (SpMV vs HBM peak, batched vs unbatched)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU oracle sample budget (s)")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the unbatched / block / learned-warm-start comparison of the posterior")
+    ap.add_argument("--cpu-probes", type=int, default=8, help="oracle probe solves in the CPU-baseline sample")
     ap.add_argument("--kernel", default=None,
                     choices=["block_iter", "spmv", "spmm", "net_forward", "net_train", "net_conv", "net_conv_mma",
                              "net_wgrad"],
@@ -143,6 +159,19 @@ def max_over_ranks(world, v: float) -> float:
     return float(t.item())
 
 
+def make_workload(args, **kw):
+    import synth
+    w = synth.make_workload(args.workload, threads=os.cpu_count() or 0, **kw)
+    K = args.K or w.K
+    return w, K
+
+
+def workload_desc(w, K, args):
+    """The workload string of the bench line's config (both arms)."""
+    return (f"{w.name}: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, {w.T} views "
+            f"{w.intr[4]}x{w.intr[5]}, K={K} probes at rel_tol {args.tol:g}, mean at rel_tol {args.mean_tol:g}")
+
+
 # ----------------------------------------------------------------- oracle
 
 def oracle_system(w):
@@ -154,55 +183,58 @@ def oracle_system(w):
     return b, qd, rhs
 
 
-def oracle_sample(w, system, tol, K, budget_s, k0=0):
-    """Time the oracle's posterior solve on a bounded sample: the mean solve
-    plus as many of the K probe solves as fit in budget_s; extrapolated
-    linearly to K probes."""
+def oracle_mean_time(w, system, tol):
     import oracle
     b, qd, rhs = system
-    cores = len(os.sched_getaffinity(0))
     t0 = time.perf_counter()
     oracle.pcg(b, w.lam, qd, rhs, tol=tol)
-    t_mean = time.perf_counter() - t0
-    t1 = time.perf_counter()
-    k = 0
-    while k < K and (k < 1 or time.perf_counter() - t1 < budget_s):
-        oracle.hutchinson(b, w.lam, qd, 1, w.seed, tol=tol, k0=(k0 + k) % K)
-        k += 1
-    t_probe = (time.perf_counter() - t1) / k
-    est = t_mean + K * t_probe
-    sample = (f"{w.name}: oracle mean solve + {k} of {K} probe solves at rel_tol {tol:g} on N={b.N} band "
-              f"voxels (FP64 CSR PCG, OpenMP over {cores} threads); time extrapolated linearly to {K} probes")
-    return est, cores, sample, k
+    return time.perf_counter() - t0
 
 
-def workload_desc(w, args):
-    """The workload string of the bench line's config (both arms)."""
-    return (f"{w.name}: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, "
-            f"{w.T} views {w.intr[4]}x{w.intr[5]}, K={args.K} probes, rel_tol {args.tol:g}")
+def oracle_probe_time(w, system, tol, k):
+    """Wall time of the oracle's solve of probe k (one Hutchinson term)."""
+    import oracle
+    b, qd, rhs = system
+    t0 = time.perf_counter()
+    oracle.hutchinson(b, w.lam, qd, 1, w.seed, tol=tol, k0=k)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_sample_desc(w, N, K, n_probes, args):
+    return (f"{w.name}: oracle (FP64 CSR PCG, OpenMP over {cpu_cores()} threads) on N={N} band voxels: the mean "
+            f"solve at rel_tol {args.mean_tol:g} and {n_probes} of the {K} probe solves at rel_tol {args.tol:g} "
+            f"timed; the posterior time is the mean solve + {K} x the mean probe-solve time (extrapolated "
+            f"linearly from the {n_probes} probes)")
 
 
 def run_reference(args, world, rank):
-    """The CPU oracle as the reference arm: each step times a bounded sample
-    of the posterior solve on the host cores (rank 0 only)."""
+    """The CPU oracle as the reference arm (rank 0 only).  Set-up (band,
+    observations, assembly, and one timing of the mean solve) is untimed;
+    each step then times one probe solve (probe k = step index), a bounded
+    sample of the workload; value = t_mean + K x the mean probe time."""
     if rank != 0:
         return
-    import synth
-    w = synth.make_workload(args.workload)
+    w, K = make_workload(args)
     system = oracle_system(w)
-    vals = []
-    cores, sample = 1, ""
-    budget = max(1.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
+    t_mean = oracle_mean_time(w, system, args.mean_tol)
+    probe = []
     for i in range(args.warmup + args.steps):
-        est, cores, sample, _ = oracle_sample(w, system, args.tol, args.K, budget, k0=i)
+        t = oracle_probe_time(w, system, args.tol, i % K)
         if i >= args.warmup:
-            vals.append(est)
-    v = statistics.mean(vals)
+            probe.append(t)
+    t_probe = statistics.mean(probe)
+    v = t_mean + K * t_probe
+    sample = oracle_sample_desc(w, system[0].N, K, len(probe), args) + \
+        f"; each step is one probe solve ({t_probe:.3f} s); the mean solve took {t_mean:.3f} s"
     line = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": workload_desc(w, args), "parallelism": f"replicas x{world}"},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+            "warmup": args.warmup, "ms_per_step": t_probe * 1e3, "higher_is_better": False,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": workload_desc(w, K, args), "parallelism": "CPU oracle on rank 0"},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -213,13 +245,13 @@ def run_ours(args, world, rank, local):
     import numpy as np
     import torch
 
-    import synth
     from paper_2602_19697_gb300 import bfsdf, build
+    from paper_2602_19697_gb300.sharding import probe_range
 
     build.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = synth.make_workload(args.workload, seed=rank)
+    w, K = make_workload(args)
     stream = torch.cuda.Stream(dev)
     ctx = bfsdf.Context(local, stream.cuda_stream)
     depth = torch.from_numpy(w.depth).to(dev)
@@ -227,6 +259,21 @@ def run_ours(args, world, rank, local):
     cand = torch.from_numpy(w.cand_poses).to(dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     R = args.rhs_block
+    k0, k1 = probe_range(rank, world, K)
+    lead = rank == 0
+
+    def variance(band, s):
+        """s for the job's K probes: this rank's share, then the sum over ranks."""
+        if world == 1:
+            return band.estimate_variance(s, K=K, seed=0, rel_tol=args.tol, rhs_block=R).iters
+        it = 0
+        if k1 > k0:
+            it = band.estimate_variance_range(s, k0, k1, seed=0, rel_tol=args.tol, rhs_block=R, scale=1.0 / K).iters
+        else:
+            s.zero_()
+        import torch.distributed as dist
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        return it
 
     def step():
         with torch.cuda.stream(stream):
@@ -241,17 +288,21 @@ def run_ours(args, world, rank, local):
         ev[2].record(stream)
         mu = torch.empty(band.N, device=dev)
         s = torch.empty(band.N, device=dev)
-        im = band.solve_mean(mu, rel_tol=args.tol)
+        im = band.solve_mean(mu, rel_tol=args.mean_tol) if lead else None
         ev[3].record(stream)
-        iv = band.estimate_variance(s, K=args.K, seed=0, rel_tol=args.tol, rhs_block=R)
+        vi = variance(band, s)
         ev[4].record(stream)
-        V, F = band.extract_surface(mu, device=dev)
+        tris, best = 0, -1
+        if lead:
+            V, F = band.extract_surface(mu, device=dev)
+            tris = int(F.shape[0])
         ev[5].record(stream)
-        U, best = band.score_views(mu, s, cand, w.cand_intr)
+        if lead:
+            U, best = band.score_views(mu, s, cand, w.cand_intr)
         ev[6].record(stream)
         stream.synchronize()
         t = [ev[i].elapsed_time(ev[i + 1]) for i in range(6)]
-        info = dict(N=band.N, NB=band.NB, mean_iters=im.iters, var_iters=iv.iters, tris=int(F.shape[0]),
+        info = dict(N=band.N, NB=band.NB, mean_iters=im.iters if im else None, var_iters=vi, tris=tris,
                     best_view=best)
         return band, t, info
 
@@ -286,17 +337,27 @@ def run_ours(args, world, rank, local):
     stepms = [sum(t) for t in times]
     post_s = max_over_ranks(world, statistics.mean(post) / 1e3)
     step_s = max_over_ranks(world, statistics.mean(stepms) / 1e3)
-    value = post_s / world                   # seconds per posterior across the job
+    value = post_s                            # one posterior per job (probes shared by the ranks)
 
-    # ---- roofline of the dominant kernel (block PCG SpMV), event-timed
+    # ---- the mean at the probes' tolerance, and the rooflines on this band (untimed for the headline)
     hbm, peak_kind = peaks()
     band = ctx.build_band_w(w, depth, poses)
     band.integrate_depth(depth, poses, w.intr)
-    R_used, tune_ms = (R, None) if R else band.autotune_rhs_block(args.K)  # the width the timed steps used
-    s = torch.empty(band.N, device=dev)
-    band.estimate_variance(s, K=R_used, seed=0, rel_tol=args.tol, rhs_block=R_used)
-    ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R_used, reps=50)
     N, NB = band.N, band.NB
+    mu = torch.empty(N, device=dev)
+    ms_mean6 = []
+    for i in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush_l2()
+        e0.record(stream)
+        i6 = band.solve_mean(mu, rel_tol=args.tol)
+        e1.record(stream)
+        stream.synchronize()
+        ms_mean6.append(e0.elapsed_time(e1))
+    R_used, tune_ms = (R, None) if R else band.autotune_rhs_block(max(k1 - k0, 1))
+    s = torch.empty(N, device=dev)
+    band.estimate_variance(s, K=R_used, seed=0, rel_tol=args.tol, rhs_block=R_used)
+    ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R_used, reps=20)
     # algorithmic bytes of one probe-solver iteration (per voxel row of R
     # columns): r, w, s, p read and p, r', s', w' written (32 B per column),
     # the correction x read and written every second iteration (4 B per
@@ -304,20 +365,16 @@ def run_ours(args, world, rank, local):
     # and 1/Q_jj read (8 B); the neighbour gathers of the SpMM are not
     # counted (they come from shared memory and L2 by design)
     bytes_it = N * (R_used * 36 + 8)
-    ms_spmv = band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=200)
-    bytes_spmv = N * 12 + NB * (128 + 24)   # x, qd read, y written; brick metadata
     achieved = bytes_it / (ms_iter * 1e-3) / 1e9
-    # DRAM bytes (read + write) per launch from one ncu capture of this kernel on this band at R = 32
-    # (ncu --set full, 2 launches): mean of an x-writing launch (938.7 MB) and an x-holding one (727.7 MB)
-    traffic = 833234944 if (R_used == 32 and N == 640524) else None
+    traffic = BLK_IT_TRAFFIC.get((N, R_used))
     roof = {"kernel": "k_blk_it<%d> (one probe-solver iteration: vector updates and w = Q u in one pass, "
                       "the dominant kernel)" % R_used, "bound": "hbm",
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": bytes_it,
-            "ms_per_launch": round(ms_iter, 5)}
-    spmv = {"kernel": "k_brick (7-point SpMV, single RHS)", "achieved": round(bytes_spmv / (ms_spmv * 1e-3) / 1e9, 1),
-            "ms_per_launch": round(ms_spmv, 5), "bytes_per_launch": bytes_spmv,
-            "note": "single-RHS vectors of this workload are L2-resident (%.1f MB)" % (N * 12 / 1e6)}
+            "ms_per_launch": round(ms_iter, 5),
+            "timing": "20 back-to-back launches between CUDA events on the library stream (working set "
+                      f"{bytes_it / 1e9:.2f} GB per launch, larger than L2)"}
+    spmv = spmv_roofline(band, stream, hbm, peak_kind)
     band.free()
 
     # ---- end to end through the C ABI: pinned host frames in, host mu and s out
@@ -327,114 +384,142 @@ def run_ours(args, world, rank, local):
         ph = torch.from_numpy(w.poses).pin_memory()
         muh = torch.empty(N, dtype=torch.float32).pin_memory()  # result buffers, allocated once
         sh = torch.empty(N, dtype=torch.float32).pin_memory()
+        sd = torch.empty(N, dtype=torch.float32, device=dev)
         e2e_t = []
         for i in range(2 + args.steps):
             stream.synchronize()
+            barrier(world)
             t0 = time.perf_counter()
             with torch.cuda.stream(stream):  # the step's inputs, copied once for the two calls that read them
                 dd = dh.to(dev, non_blocking=True)
                 pd = ph.to(dev, non_blocking=True)
-            b = ctx.build_band_w(w, dd, pd)
-            b.integrate_depth(dd, pd, w.intr)
-            if b.N != N:
-                raise RuntimeError("band size differs between runs")
-            b.solve_mean(muh, rel_tol=args.tol)
-            b.estimate_variance(sh, K=args.K, seed=0, rel_tol=args.tol, rhs_block=R)
+                b = ctx.build_band_w(w, dd, pd)
+                b.integrate_depth(dd, pd, w.intr)
+                if b.N != N:
+                    raise RuntimeError("band size differs between runs")
+                if lead:
+                    b.solve_mean(muh, rel_tol=args.mean_tol)
+                if world == 1:
+                    b.estimate_variance(sh, K=K, seed=0, rel_tol=args.tol, rhs_block=R)
+                else:
+                    variance(b, sd)
+                    if lead:
+                        sh.copy_(sd, non_blocking=True)
             stream.synchronize()
             dt = time.perf_counter() - t0
             if i >= 2:
                 e2e_t.append(dt)
             b.free()
-        e2e_s = max_over_ranks(world, statistics.mean(e2e_t)) / world
+        e2e_s = max_over_ranks(world, statistics.mean(e2e_t))
         e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(w.depth.nbytes + w.poses.nbytes),
                "d2h_bytes_per_step": int(2 * N * 4),
-               "note": "pinned host frames copied to the device once, then build_band + integrate_depth + "
-                       "solve_mean + estimate_variance through the C ABI, mu and s written to pinned host memory"}
+               "note": "pinned host frames copied to the device once per step, then build_band + integrate_depth "
+                       "+ solve_mean + estimate_variance through the C ABI, mu and s written to pinned host memory"}
 
-    obj = None
-    if world == 1 and not args.no_object:
-        obj = object_sequence(ctx, stream, args.tol, hbm, peak_kind)
+    cmp_ = None
+    if world == 1 and not args.no_compare:
+        cmp_ = compare_forms(ctx, stream, w, K, args, flush_l2)
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        est, cores, sample, k = oracle_sample(w, oracle_system(w), args.tol, args.K, args.cpu_seconds)
-        cpu = {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample}
+    if lead and not args.no_cpu_baseline:
+        system = oracle_system(w)
+        t_mean = oracle_mean_time(w, system, args.mean_tol)
+        tp = [oracle_probe_time(w, system, args.tol, k) for k in range(min(args.cpu_probes, K))]
+        est = t_mean + K * statistics.mean(tp)
+        cpu = {"value": est, "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": oracle_sample_desc(w, N, K, len(tp), args)}
 
-    if rank == 0:
+    if lead:
         mean_t = [statistics.mean(x) for x in zip(*times)]
         line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload_desc(w, args),
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_desc(w, K, args),
                            "N_band": info["N"], "bricks": info["NB"], "rhs_block": R_used,
                            "rhs_block_choice": "autotuned" if not R else "fixed",
                            "autotune_ms_per_iter_r8_r16_r32": None if tune_ms is None else [round(float(v), 5) for v in tune_ms],
-                           "l2": "512 MB buffer written between timed steps",
-                           "parallelism": f"replicas x{world}"},
+                           "l2": "inputs larger than L2 (the probe block's vectors are several GB) and a 512 MB "
+                                 "buffer written between timed steps",
+                           "parallelism": "single GPU" if world == 1 else f"probes sharded over {world} ranks, "
+                                                                            "one NCCL all-reduce of s"},
                 "breakdown_ms": {"build_band": mean_t[0], "integrate_depth": mean_t[1],
                                  "solve_mean": mean_t[2], "estimate_variance": mean_t[3],
-                                 "extract_surface": mean_t[4], "score_views": mean_t[5]},
-                "iters": {"mean": info["mean_iters"], "variance_total": info["var_iters"]},
-                "roofline": roof, "spmv": spmv, "object_sequence": obj, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "wall_s": round(wall, 3)}
+                                 "extract_surface": mean_t[4], "score_views": mean_t[5],
+                                 "solve_mean_at_probe_tol": round(statistics.median(ms_mean6), 4)},
+                "iters": {"mean": info["mean_iters"], "mean_at_probe_tol": i6.iters,
+                          "variance_total": info["var_iters"]},
+                "roofline": roof, "spmv": spmv, "compare": cmp_, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clocks, "wall_s": round(wall, 3)}
         print(json.dumps(line), flush=True)
 
 
-def object_sequence(ctx, stream, tol, hbm, peak_kind):
-    """The 200-frame object sequence (512^3 blob, band +-24, 7.2 M voxels):
-    single-RHS SpMV against the HBM peak (L2 written between launches, median
-    of 20), and time to posterior (mean + 128-probe variance at tol) in three
-    forms: the probes one at a time (unbatched single-RHS PCG), block PCG, and
-    block PCG with the mean warm-started by the learned network (trained here
-    on seeded sphere instances) and the network's variance surrogate judged."""
+def spmv_roofline(band, stream, hbm, peak_kind):
+    """Single-RHS SpMV on the band: single launches after writing and then
+    reading 1 GB (L2 flushed, its dirty lines written back), median of 20."""
     import numpy as np
+    import torch
+
+    from paper_2602_19697_gb300 import bfsdf
+    dev = torch.device("cuda", torch.cuda.current_device())
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device=dev)
+    clean = torch.zeros(256 * 1024 * 1024, dtype=torch.float32, device=dev)
+    band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=3)
+    ms = []
+    for i in range(20):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            clean.sum()
+        stream.synchronize()
+        ms.append(band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=1))
+    nbytes = band.N * 12 + band.NB * 152
+    gbs = nbytes / (float(np.median(ms)) * 1e-3) / 1e9
+    del flush, clean
+    return {"kernel": "k_spmv (7-point SpMV, single RHS)", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(gbs / hbm, 4), "peak_kind": peak_kind, "ms_median": round(float(np.median(ms)), 5),
+            "bytes": nbytes, "bytes_per_voxel": round(nbytes / band.N, 3),
+            "l2": "1 GB written, then another 1 GB read, before each of 20 single launches; median"}
+
+
+def compare_forms(ctx, stream, w, K, args, flush_l2):
+    """Time to posterior on the same band in three forms, each run twice and
+    the second run reported: the probes one at a time (unbatched single-RHS
+    PCG), block PCG at the autotuned width, and block PCG with the mean
+    warm-started by the learned network (trained here on seeded sphere
+    instances) and the network's variance surrogate judged by 16 probes."""
     import torch
 
     import synth
     from paper_2602_19697_gb300 import bfsdf, learned
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = synth.make_workload("blob512", threads=os.cpu_count() or 0)
     depth, poses = torch.from_numpy(w.depth).to(dev), torch.from_numpy(w.poses).to(dev)
     band = ctx.build_band_w(w, depth, poses)
     band.integrate_depth(depth, poses, w.intr)
-    N, NB = band.N, band.NB
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device=dev)
-    clean = torch.zeros(256 * 1024 * 1024, dtype=torch.float32, device=dev)
-    ms = []
-    for i in range(20):
-        # write 1 GB (evicts the band's data from L2), then read another 1 GB, so that the dirty lines of
-        # the flush are written back before the timed launch instead of during it
-        with torch.cuda.stream(stream):
-            flush.fill_(float(i))
-            clean.sum()
-        stream.synchronize()
-        ms.append(band.bench_kernel(bfsdf.BF_KERNEL_SPMV, reps=1))
-    nbytes = N * 12 + NB * 152
-    spmv_gbs = nbytes / (float(np.median(ms)) * 1e-3) / 1e9
+    N = band.N
 
     def posterior(rhs_block, net=None):
         with torch.cuda.stream(stream):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             mu, s = torch.empty(N, device=dev), torch.empty(N, device=dev)
-            flush.zero_()
+            flush_l2()
             e0.record(stream)
             if net is None:
-                im = band.solve_mean(mu, rel_tol=tol)
-                iv = band.estimate_variance(s, K=128, seed=0, rel_tol=tol, rhs_block=rhs_block)
+                im = band.solve_mean(mu, rel_tol=args.tol)
+                iv = band.estimate_variance(s, K=K, seed=0, rel_tol=args.tol, rhs_block=rhs_block)
                 acc = None
             else:
                 lsh = torch.empty(N, device=dev)
                 net.forward(band, mu, lsh)
-                im = band.solve_mean(mu, rel_tol=tol, warm=True)
-                iv, _, _, acc = band.surrogate_variance(lsh, s, K=128, K_judge=16, seed=0, rel_tol=tol,
+                im = band.solve_mean(mu, rel_tol=args.tol, warm=True)
+                iv, _, _, acc = band.surrogate_variance(lsh, s, K=K, K_judge=16, seed=0, rel_tol=args.tol,
                                                         rhs_block=rhs_block)
             e1.record(stream)
             stream.synchronize()
         return e0.elapsed_time(e1), im.iters, iv.iters, acc
 
+    posterior(1)
     plain_ms, plain_mi, plain_vi, _ = posterior(1)
-    posterior(0)  # the autotuner chooses the block width here (and for the judge's and remaining probes below)
+    posterior(0)
     block_ms, block_mi, block_vi, _ = posterior(0)
     data = [learned.make_example(ctx, synth.make_workload("sphere64", variant=i)) for i in range(50)]
     net = bfsdf.Net(ctx, seed=0)
@@ -442,18 +527,12 @@ def object_sequence(ctx, stream, tol, hbm, peak_kind):
     posterior(0, net)
     warm_ms, warm_mi, warm_vi, acc = posterior(0, net)
     band.free()
-    return {"workload": f"blob512: {w.n}^3 grid at {w.h * 1e3:g} mm, band +-{w.band_vox:g}, {w.T} views "
-                        f"{w.intr[4]}x{w.intr[5]}, K=128 probes, rel_tol {tol:g}",
-            "N_band": N, "bricks": NB,
-            "spmv": {"kernel": "k_spmv (7-point SpMV, single RHS, brick tiles with shared-memory halo)",
-                     "achieved": round(spmv_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(spmv_gbs / hbm, 4),
-                     "peak_kind": peak_kind, "ms_median": round(float(np.median(ms)), 5), "bytes": nbytes,
-                     "l2": "1 GB written, then another 1 GB read, before each of 20 single launches; median"},
+    return {"note": "time to posterior (mean + variance, both at rel_tol %g), each form run twice, second run" % args.tol,
             "posterior_ms": {"unbatched_single_rhs_pcg": round(plain_ms, 3), "block_pcg_autotuned": round(block_ms, 3),
                              "block_pcg_learned_warm_start": round(warm_ms, 3)},
             "iters": {"unbatched": [plain_mi, plain_vi], "block": [block_mi, block_vi],
                       "learned": [warm_mi, warm_vi]},
-            "surrogate_bricks_accepted": acc}
+            "surrogate_bricks_accepted": acc, "bricks": band.NB}
 
 
 def kernel_workload(name):

@@ -571,6 +571,9 @@ static int pcg_csr(const csr* A, const double* diag, const double* b, const doub
   double* q = (double*)malloc(sizeof(double) * (N ? N : 1));
   int status = 1, it = 0, restarts = 0;
   double bn = sqrt(dot(N, b, b));
+#ifdef _OPENMP
+  #pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < N; ++i) x[i] = x0 ? x0[i] : 0.0;
   if (bn == 0.0) {
     for (int64_t i = 0; i < N; ++i) x[i] = 0.0;
@@ -581,9 +584,15 @@ static int pcg_csr(const csr* A, const double* diag, const double* b, const doub
   }
   for (;;) {
     csr_mv(A, x, q);
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < N; ++i) r[i] = b[i] - q[i];
     double rn = sqrt(dot(N, r, r));
     if (rn <= tol * bn) { status = 0; break; }
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < N; ++i) { z[i] = r[i] / diag[i]; p[i] = z[i]; }
     double rho = dot(N, r, z);
     int conv = 0;
@@ -593,13 +602,22 @@ static int pcg_csr(const csr* A, const double* diag, const double* b, const doub
       ++it;
       if (!(pq > 0.0)) { status = 2; break; }
       double alpha = rho / pq;
+#ifdef _OPENMP
+      #pragma omp parallel for schedule(static)
+#endif
       for (int64_t i = 0; i < N; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
       rn = sqrt(dot(N, r, r));
       if (rn <= tol * bn) { conv = 1; break; }
+#ifdef _OPENMP
+      #pragma omp parallel for schedule(static)
+#endif
       for (int64_t i = 0; i < N; ++i) z[i] = r[i] / diag[i];
       double rho2 = dot(N, r, z);
       double beta = rho2 / rho;
       rho = rho2;
+#ifdef _OPENMP
+      #pragma omp parallel for schedule(static)
+#endif
       for (int64_t i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
     }
     if (status == 2 || !conv) break;
@@ -607,6 +625,9 @@ static int pcg_csr(const csr* A, const double* diag, const double* b, const doub
     if (++restarts > 3) break;
   }
   csr_mv(A, x, q);
+#ifdef _OPENMP
+  #pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < N; ++i) r[i] = b[i] - q[i];
   double rt = sqrt(dot(N, r, r)) / bn;
   if (status != 2) status = (rt <= tol) ? 0 : 1;
@@ -643,6 +664,9 @@ static double rademacher(uint64_t seed, uint64_t k, uint64_t lin) {
 }
 
 void bfo_probe(uint64_t seed, uint64_t k, int64_t n, const int64_t* lin, double* z) {
+#ifdef _OPENMP
+  #pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < n; ++i) z[i] = rademacher(seed, k, (uint64_t)lin[i]);
 }
 
@@ -667,9 +691,15 @@ int bfo_hutchinson(const bfo_band* B, double lam, const double* qdiag, int K, ui
     int st = pcg_csr(&A, qdiag, z, NULL, tol, max_iter, u, &it, &rr);
     if (st > worst) worst = st;
     tot += it;
+#ifdef _OPENMP
+    #pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < N; ++i) s[i] += z[i] * u[i];
     if (per_probe && k < n_keep) memcpy(per_probe + (int64_t)k * N, u, sizeof(double) * N);
   }
+#ifdef _OPENMP
+  #pragma omp parallel for schedule(static)
+#endif
   for (int64_t i = 0; i < N; ++i) s[i] /= K;
   *total_iters = tot;
   free(z); free(u);

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_prints_one_contract_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "sphere64",
-                        "--steps", "1", "--warmup", "0", "--cpu-seconds", "1"], capture_output=True, text=True,
+                        "--steps", "2", "--warmup", "0"], capture_output=True, text=True,
                        cwd=ROOT, timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.strip()]
@@ -23,3 +23,5 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert d["config"]["workload"].startswith("sphere64: 64^3 grid at 15 mm")
+    # each step is one probe solve: the steps' time is what the run spent, the value extrapolates to K probes
+    assert d["ms_per_step"] > 0 and d["value"] >= 16 * d["ms_per_step"] * 1e-3

@@ -96,3 +96,26 @@ def test_full_view_scores(full):
                                    w.sig_a, w.sig_b, w.sig_pose, w.sig_model)
     np.testing.assert_allclose(U, Uo, rtol=1e-3, atol=1e-6 * Uo.max())
     assert best == besto or Uo[best] >= Uo[besto] * (1 - 1e-3)
+
+
+def test_batched_variance_config_sphere64_k256():
+    """The batched-variance workload: the sphere64 scene with 256 probes as
+    block PCG at the autotuned width (BF16 probes, FP64 inner products,
+    float-float refinement), rel_tol 1e-6, against the oracle's 256-probe
+    estimate (1e-12) at every band voxel."""
+    w = synth.make_workload("sphere64_k256")
+    assert w.K == 256
+    ob = oracle.build_band_w(w)
+    d, hd, _ = oracle.integrate_w(ob, w)
+    qd, rhs = oracle.assemble(ob, d, hd, w.lam, w.lam_b)
+    so, st, _, _ = oracle.hutchinson(ob, w.lam, qd, w.K, w.seed, tol=1e-12)
+    assert st == 0
+    gb, depth, poses = gpu_band(w)
+    gb.integrate_depth(depth, poses, w.intr)
+    R, ms = gb.autotune_rhs_block(w.K)
+    assert R in (8, 16, 32)
+    s = torch.empty(gb.N, device="cuda")
+    info = gb.estimate_variance(s, K=w.K, seed=w.seed, rel_tol=1e-6, rhs_block=0)
+    assert info.iters >= w.K
+    rel = np.abs(s.cpu().numpy() - so) / np.maximum(np.abs(so), 1.0 / qd)
+    assert rel.max() <= 1e-3, rel.max()

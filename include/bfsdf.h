@@ -145,6 +145,33 @@ bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* band, const float* depth, int
  * Totals must stay below 2^31 in magnitude.  Unknown flags: BF_EINVAL. */
 #define BF_INTEGRATE_DETERMINISTIC 1u
 
+/* Trilinear observation rows (Sec. 3.5: each observation is a linear row over
+ * the voxel values with up to 8 non-zeros, the trilinear interpolation
+ * weights of the sample point; Sec. 3.6 precision equation: A^T W A then
+ * couples each voxel with its 26 neighbours, so Q is a 27-point stencil with
+ * per-voxel coefficients).  Flag of bf_integrate_depth_ex: the band
+ * accumulates these rows instead of the voxel-binned ones.
+ *   Samples: on every valid pixel's ray at s_p + k h for the integers k with
+ *   |k| <= floor(band_vox) (2b + 1 per ray), observed value y = -k voxels
+ *   (the projective SDF with n = -ray direction), precision w as in
+ *   bf_integrate_depth.  Row: the weights of the sample in the cell of the 8
+ *   voxel centres around it; used when every corner with a non-zero weight is
+ *   a band voxel.  The cell and the weights follow an FP32 specification
+ *   (each operation rounded separately, in this order): dx = ((u + 0.5) -
+ *   cx)/fx, dy likewise, nrm = sqrt((dx dx + dy dy) + 1), r_i = ((R_i0 dx +
+ *   R_i1 dy) + R_i2)/nrm, s = D nrm + k h, q_i = C_i + s r_i, g_i = (q_i -
+ *   o_i)/h - 0.5, i0 = floor(g), f = g - i0, corner weight (w_x w_y) w_z with
+ *   w = f (upper corner) or 1 - f (lower corner).
+ *   Then bf_spmv, bf_solve_mean (FP32 PCG corrections inside FP64 refinement;
+ *   no BF_SOLVE_WARM), bf_estimate_variance[_range] (blocks of 8 probes:
+ *   rhs_block 0 or 8) and bf_export_system use the 27-point Q; bf_spmm,
+ *   bf_solve_mean_static, bf_score_views_exact, bf_surrogate_variance,
+ *   bf_autotune_rhs_block and bf_bench_kernel's block iteration return
+ *   BF_ESTATE.  Not combinable with BF_INTEGRATE_DETERMINISTIC (BF_EINVAL); a
+ *   band keeps one kind of rows until bf_reset_observations (the other kind:
+ *   BF_ESTATE). */
+#define BF_INTEGRATE_TRILINEAR 2u
+
 /* The observation sums d = sum w and hdata = sum w y in FP64 ([N] double
  * each, device or host; NULL skips): after deterministic integration the
  * int64 fixed-point totals converted exactly (to 53 bits), else the FP32
@@ -152,6 +179,24 @@ bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* band, const float* depth, int
 bf_status bf_export_observations_f64(bf_ctx* ctx, const bf_band* band, double* d, double* hdata);
 bf_status bf_integrate_depth_ex(bf_ctx* ctx, bf_band* band, const float* depth, int T, const float* poses,
                                 const bf_intrinsics* K, unsigned flags);
+
+/* The trilinear rows of frames (depth [T][H][W], poses [T][3][4] as in
+ * bf_integrate_depth; the band's own frames or any others), for checking the
+ * FP32 specification above: M = T H W (2b + 1) rows in the order (frame,
+ * pixel row by row, k = -b .. b); idx [M][8] int32 compact indices of the
+ * cell corners (corner c at offset (c & 1, (c >> 1) & 1, (c >> 2) & 1) from
+ * the cell's lowest centre; 0 for a zero-weight corner off the band), wts
+ * [M][8] float weights, used [M] uint8; unused rows (invalid pixels
+ * included) have idx and wts 0.  *M (host) receives M; with idx, wts and used
+ * all NULL only M is returned (else all three are needed: BF_EINVAL). */
+bf_status bf_export_trilinear_rows(bf_ctx* ctx, const bf_band* band, const float* depth, int T, const float* poses,
+                                   const bf_intrinsics* K, int32_t* idx, float* wts, uint8_t* used, int64_t* M);
+
+/* The 27-point precision of a band with trilinear rows (Sec. 3.6 precision
+ * equation): coef [27][N] float, coef[o][j] = Q_{j, j + off(o)} with off(o) =
+ * (o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1) in (i, j, k) voxel steps, 0 where
+ * that neighbour is not a band voxel.  BF_ESTATE for other bands. */
+bf_status bf_export_precision27(bf_ctx* ctx, const bf_band* band, float* coef);
 
 /* Reset the accumulated observations of a band to zero. */
 bf_status bf_reset_observations(bf_ctx* ctx, bf_band* band);

@@ -3,9 +3,8 @@ up to 8 non-zeros per row for trilinear interpolation) and the posterior
 system they give (Sec. 3.6: Q = Q0 + A^T W A, h = A^T W y + b0).
 
 TEST INFRASTRUCTURE: the FP64 reference of the trilinear form of the
-observation model, which the CUDA path does not implement yet (its rows are
-voxel-binned, one non-zero each, so its Q stays 7-point).  Only tests may use
-this module.
+observation model (the CUDA path's BF_INTEGRATE_TRILINEAR rows and 27-point
+precision are checked against it).  Only tests may use this module.
 
 Readings (where Sec. 3.5 leaves the sample placement open):
   * a valid pixel (depth D > 0 and finite) gives the ray r = R d_c / |d_c|,
@@ -107,21 +106,41 @@ def trilinear_rows(band, q, cmap=None):
     return idx, wts, used
 
 
-def system(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, sig_pose=0.0, sig_model=0.0):
+def sample_precisions(depth, band_vox, h, sig_a, sig_b, sig_pose=0.0, sig_model=0.0):
+    """w [M] of the samples of ``rows_fp32`` (same order: frames, valid pixels row by row, k), in FP64 from the
+    measured depth: h^2 / ((sig_a + sig_b D^2)^2 + sig_pose^2 + sig_model^2)."""
+    b = int(np.floor(band_vox + 1e-9))
+    out = []
+    for Dt in np.asarray(depth, np.float32):
+        D = Dt[np.isfinite(Dt) & (Dt > 0)].astype(np.float64)
+        sig2 = (sig_a + sig_b * D ** 2) ** 2 + sig_pose ** 2 + sig_model ** 2
+        out.append(np.repeat(h * h / sig2, 2 * b + 1))
+    return np.concatenate(out) if out else np.zeros(0)
+
+
+def system(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, sig_pose=0.0, sig_model=0.0, rows="fp64"):
     """(Q scipy CSR [N,N], h [N], d [N] = A^T w, number of used samples): the posterior precision and information
-    vector with trilinear observation rows."""
+    vector with trilinear observation rows.  rows="fp64": cells and weights from the FP64 sample points
+    (``samples``, ``trilinear_rows``); rows="fp32": the rows of the FP32 specification (``rows_fp32``), the form a
+    kernel reproduces bit for bit (the two differ only for samples within rounding of a cell boundary); the sums
+    are FP64 either way."""
     import scipy.sparse
 
     from . import csr
-    q, y, w = samples(depth, poses, intr, band.h, band_vox, sig_a, sig_b, sig_pose, sig_model)
-    idx, wts, used = trilinear_rows(band, q)
+    if rows == "fp32":
+        idx, wts, used, y = rows_fp32(band, depth, poses, intr, band_vox)
+        w = sample_precisions(depth, band_vox, band.h, sig_a, sig_b, sig_pose, sig_model)
+        wts = wts.astype(np.float64)
+    else:
+        q, y, w = samples(depth, poses, intr, band.h, band_vox, sig_a, sig_b, sig_pose, sig_model)
+        idx, wts, used = trilinear_rows(band, q)
     idx, wts, y, w = idx[used], wts[used], y[used], w[used]
     N = band.N
     # A^T W A: for every row, w a a^T over its 8 x 8 corner pairs
-    rows = np.repeat(idx, 8, axis=1).reshape(-1)
-    cols = np.tile(idx, (1, 8)).reshape(-1)
+    ri = np.repeat(idx, 8, axis=1).reshape(-1)
+    ci = np.tile(idx, (1, 8)).reshape(-1)
     vals = (w[:, None, None] * wts[:, :, None] * wts[:, None, :]).reshape(-1)
-    AtWA = scipy.sparse.coo_matrix((vals, (rows, cols)), shape=(N, N)).tocsr()
+    AtWA = scipy.sparse.coo_matrix((vals, (ri, ci)), shape=(N, N)).tocsr()
     d = np.bincount(idx.reshape(-1), weights=(w[:, None] * wts).reshape(-1), minlength=N)
     hd = np.bincount(idx.reshape(-1), weights=(w[:, None] * wts * y[:, None]).reshape(-1), minlength=N)
     bd = np.asarray(band.bdry, np.float64)
@@ -190,13 +209,14 @@ def rows_fp32(band, depth, poses, intr, band_vox, cmap=None):
 
 
 def posterior(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, K, seed, tol=1e-12, sig_pose=0.0,
-              sig_model=0.0):
+              sig_model=0.0, rows="fp64"):
     """(mu [N], s [N]) under trilinear rows: the MAP mean Q mu = h (sparse direct solve) and the K-probe estimate
-    s = (1/K) sum_k z_k (.) Q^-1 z_k with the probes of ``oracle.probe`` (block PCG over the K columns)."""
+    s = (1/K) sum_k z_k (.) Q^-1 z_k with the probes of ``oracle.probe`` (block PCG over the K columns); rows as in
+    ``system``."""
     import scipy.sparse.linalg
 
     from . import block_pcg, probe
-    Q, hv, _, _ = system(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, sig_pose, sig_model)
+    Q, hv, _, _ = system(band, depth, poses, intr, band_vox, sig_a, sig_b, lam, lam_b, sig_pose, sig_model, rows)
     mu = scipy.sparse.linalg.spsolve(Q.tocsc(), hv)
     Z = np.stack([probe(seed, k, band.lin) for k in range(K)], 1)
     X, st, _ = block_pcg(band, lam, None, Z, tol=tol, Q=Q)

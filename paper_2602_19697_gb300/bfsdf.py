@@ -36,8 +36,9 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_score_views", "bf_score_views_exact", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
             "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
             "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance",
-            "bf_net_bench", "bf_autotune_rhs_block"]
+            "bf_net_bench", "bf_autotune_rhs_block", "bf_export_trilinear_rows", "bf_export_precision27"]
 BF_INTEGRATE_DETERMINISTIC = 1
+BF_INTEGRATE_TRILINEAR = 2
 BF_KERNEL_SPMV = 0
 BF_KERNEL_BLOCK_ITER = 1
 BF_KERNEL_SPMM = 2
@@ -121,6 +122,9 @@ def load_library(path: str = LIB_PATH):
                                       ctypes.POINTER(i), ctypes.POINTER(i)]),
         "bf_net_bench": (i, [vp, vp, vp, i, i, ctypes.POINTER(d)]),
         "bf_autotune_rhs_block": (i, [vp, vp, i, i, ctypes.POINTER(i), vp]),
+        "bf_export_trilinear_rows": (i, [vp, vp, vp, i, vp, ctypes.POINTER(Intrinsics), vp, vp, vp,
+                                         ctypes.POINTER(i64)]),
+        "bf_export_precision27": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -255,8 +259,14 @@ class Band:
                                                    _ptr(out["mask"])), "bf_export_band")
         return out
 
-    def integrate_depth(self, depth, poses, K, deterministic=False):
-        """Accumulate the frames' observations; deterministic=True sums them in int64 fixed point."""
+    def integrate_depth(self, depth, poses, K, deterministic=False, trilinear=False):
+        """Accumulate the frames' observations; deterministic=True sums them in int64 fixed point;
+        trilinear=True uses the trilinear rows (27-point precision)."""
+        if trilinear:
+            self.ctx.check(self.ctx.lib.bf_integrate_depth_ex(self.ctx._p, self._p, _ptr(depth), int(depth.shape[0]),
+                                                              _ptr(poses), ctypes.byref(_intr(K)),
+                                                              BF_INTEGRATE_TRILINEAR), "bf_integrate_depth_ex")
+            return
         if deterministic:
             self.ctx.check(self.ctx.lib.bf_integrate_depth_ex(self.ctx._p, self._p, _ptr(depth), int(depth.shape[0]),
                                                               _ptr(poses), ctypes.byref(_intr(K)),
@@ -271,6 +281,26 @@ class Band:
         self.ctx.check(self.ctx.lib.bf_export_observations_f64(self.ctx._p, self._p, _ptr(d), _ptr(hd)),
                        "bf_export_observations_f64")
         return d, hd
+
+    def export_trilinear_rows(self, depth, poses, K):
+        """(idx [M,8] int32, wts [M,8] float32, used [M] bool) of the frames' trilinear rows
+        (bf_export_trilinear_rows), M = T H W (2b + 1) in the order (frame, pixel, k)."""
+        M = ctypes.c_int64()
+        args = (self.ctx._p, self._p, _ptr(depth), int(depth.shape[0]), _ptr(poses), ctypes.byref(_intr(K)))
+        self.ctx.check(self.ctx.lib.bf_export_trilinear_rows(*args, None, None, None, ctypes.byref(M)),
+                       "bf_export_trilinear_rows")
+        idx = np.empty((M.value, 8), np.int32)
+        wts = np.empty((M.value, 8), np.float32)
+        used = np.empty(M.value, np.uint8)
+        self.ctx.check(self.ctx.lib.bf_export_trilinear_rows(*args, _ptr(idx), _ptr(wts), _ptr(used),
+                                                             ctypes.byref(M)), "bf_export_trilinear_rows")
+        return idx, wts, used.astype(bool)
+
+    def export_precision27(self):
+        """coef [27, N] float32 (bf_export_precision27)."""
+        out = np.empty((27, self.N), np.float32)
+        self.ctx.check(self.ctx.lib.bf_export_precision27(self.ctx._p, self._p, _ptr(out)), "bf_export_precision27")
+        return out
 
     def reset_observations(self):
         self.ctx.check(self.ctx.lib.bf_reset_observations(self.ctx._p, self._p), "bf_reset_observations")

@@ -185,7 +185,8 @@ void bf_band_free(bf_band* b) {
   enter_device(b->device);
   cudaStreamSynchronize(b->stream);
   void* ptrs[] = {b->dir, b->bcoord, b->meta, b->off, b->nbr, b->lin, b->tsdf, b->wcount, b->info,
-                  b->d, b->hd, b->qd, b->rhs, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot, b->dfx, b->hfx};
+                  b->d, b->hd, b->qd, b->rhs, b->nb6, b->sp_ext, b->sp_ne, b->sp_slot, b->dfx, b->hfx,
+                  b->c27, b->q27};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -248,10 +249,17 @@ bf_status bf_integrate_depth_ex(bf_ctx* ctx, bf_band* b, const float* depth, int
   if (!ctx || !b) return BF_EINVAL;
   if (!depth || !poses || T < 1 || !valid_intr(K))
     return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth: null pointer, T < 1 or bad intrinsics");
-  if (flags & ~BF_INTEGRATE_DETERMINISTIC) return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth_ex: unknown flags");
+  if (flags & ~(BF_INTEGRATE_DETERMINISTIC | BF_INTEGRATE_TRILINEAR))
+    return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth_ex: unknown flags");
+  if ((flags & BF_INTEGRATE_DETERMINISTIC) && (flags & BF_INTEGRATE_TRILINEAR))
+    return bf_fail(ctx, BF_EINVAL, "bf_integrate_depth_ex: trilinear rows have no deterministic mode");
   const float *d_depth, *d_poses;
   BF_TRY(stage_in(ctx, depth, (size_t)T * K->H * K->W, WS_STAGE0, &d_depth));
   BF_TRY(stage_in(ctx, poses, (size_t)T * 12, WS_STAGE1, &d_poses));
+  if (flags & BF_INTEGRATE_TRILINEAR) return tri_integrate(ctx, b, d_depth, T, d_poses, to_intr(K));
+  if (b->obs_mode == 3)
+    return bf_fail(ctx, BF_ESTATE, "bf_integrate_depth: the band accumulates trilinear rows since its last "
+                                   "bf_reset_observations");
   return band_integrate(ctx, b, d_depth, T, d_poses, to_intr(K), (flags & BF_INTEGRATE_DETERMINISTIC) != 0);
 }
 
@@ -268,6 +276,7 @@ bf_status bf_reset_observations(bf_ctx* ctx, bf_band* b) {
     BF_CK(cudaMemsetAsync(b->dfx, 0, (b->N ? b->N : 1) * sizeof(int64_t), ctx->stream));
     BF_CK(cudaMemsetAsync(b->hfx, 0, (b->N ? b->N : 1) * sizeof(int64_t), ctx->stream));
   }
+  if (b->c27) BF_CK(cudaMemsetAsync(b->c27, 0, (size_t)14 * (b->N ? b->N : 1) * sizeof(float), ctx->stream));
   if (b->d) {
     BF_CK(cudaMemsetAsync(b->d, 0, b->N * 4, ctx->stream));
     BF_CK(cudaMemsetAsync(b->hd, 0, b->N * 4, ctx->stream));
@@ -326,6 +335,7 @@ bf_status bf_spmm(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y) {
   if (!ctx || !b || !X || !Y) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_spmm: call bf_integrate_depth first");
   if (R != 8 && R != 16 && R != 32) return bf_fail(ctx, BF_EINVAL, "bf_spmm: R must be 8, 16 or 32");
+  if (b->obs_mode == 3) return bf_fail(ctx, BF_ESTATE, "bf_spmm: the band holds trilinear rows (27-point Q)");
   const float* dX;
   float* dY;
   bool host;
@@ -343,12 +353,15 @@ bf_status bf_solve_mean(bf_ctx* ctx, bf_band* b, double rel_tol, int max_iter, u
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_solve_mean: call bf_integrate_depth first");
   if (!(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
     return bf_fail(ctx, BF_EINVAL, "bf_solve_mean: need 0 < rel_tol < 1 and 1 <= max_iter <= 1e7");
+  if (b->obs_mode == 3 && (flags & BF_SOLVE_WARM))
+    return bf_fail(ctx, BF_EINVAL, "bf_solve_mean: no warm start with trilinear rows");
   float* dmu;
   bool host;
   BF_TRY(stage_out(ctx, mu, b->N, WS_OUT0, &dmu, &host));
   if ((flags & BF_SOLVE_WARM) && host && b->N)
     BF_CK(cudaMemcpyAsync(dmu, mu, b->N * 4, cudaMemcpyHostToDevice, ctx->stream));
-  bf_status st = solve_mean_impl(ctx, b, rel_tol, max_iter, flags, dmu, iters, rel_res);
+  bf_status st = b->obs_mode == 3 ? tri_solve_mean(ctx, b, rel_tol, max_iter, dmu, iters, rel_res)
+                                  : solve_mean_impl(ctx, b, rel_tol, max_iter, flags, dmu, iters, rel_res);
   if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
     bf_status c = copy_out(ctx, mu, (const float*)dmu, b->N, host);
     if (c != BF_OK) return c;
@@ -365,10 +378,14 @@ bf_status bf_estimate_variance(bf_ctx* ctx, bf_band* b, int K, uint64_t seed, do
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: need K >= 1, 0 < rel_tol < 1, 1 <= max_iter <= 1e7");
   if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: rhs_block must be 0, 1, 8, 16 or 32");
+  if (b->obs_mode == 3 && rhs_block != 0 && rhs_block != TRI_R)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance: trilinear rows take rhs_block 0 or 8");
   float* ds;
   bool host;
   BF_TRY(stage_out(ctx, s, b->N, WS_OUT1, &ds, &host));
-  bf_status st = variance_impl(ctx, b, 0, K, 1.0 / K, seed, rel_tol, max_iter, rhs_block, flags, ds, total_iters);
+  bf_status st = b->obs_mode == 3
+                     ? tri_variance(ctx, b, 0, K, 1.0 / K, seed, rel_tol, max_iter, ds, total_iters)
+                     : variance_impl(ctx, b, 0, K, 1.0 / K, seed, rel_tol, max_iter, rhs_block, flags, ds, total_iters);
   if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
     bf_status c = copy_out(ctx, s, (const float*)ds, b->N, host);
     if (c != BF_OK) return c;
@@ -388,11 +405,15 @@ bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* b, int k_begin, int k
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: scale must be finite and > 0");
   if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
     return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: rhs_block must be 0, 1, 8, 16 or 32");
+  if (b->obs_mode == 3 && rhs_block != 0 && rhs_block != TRI_R)
+    return bf_fail(ctx, BF_EINVAL, "bf_estimate_variance_range: trilinear rows take rhs_block 0 or 8");
   float* ds;
   bool host;
   BF_TRY(stage_out(ctx, s_sum, b->N, WS_OUT1, &ds, &host));
-  bf_status st = variance_impl(ctx, b, k_begin, k_end, scale, seed, rel_tol, max_iter, rhs_block, flags, ds,
-                               total_iters);
+  bf_status st = b->obs_mode == 3
+                     ? tri_variance(ctx, b, k_begin, k_end, scale, seed, rel_tol, max_iter, ds, total_iters)
+                     : variance_impl(ctx, b, k_begin, k_end, scale, seed, rel_tol, max_iter, rhs_block, flags, ds,
+                                     total_iters);
   if (st == BF_OK || st == BF_NOT_CONVERGED || st == BF_BREAKDOWN) {
     bf_status c = copy_out(ctx, s_sum, (const float*)ds, b->N, host);
     if (c != BF_OK) return c;
@@ -447,11 +468,55 @@ bf_status bf_score_views_exact(bf_ctx* ctx, bf_band* b, const float* mu, const f
   if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)
     return bf_fail(ctx, BF_EINVAL, "bf_score_views_exact: rhs_block must be 0, 1, 8, 16 or 32");
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_score_views_exact: call bf_integrate_depth first");
+  if (b->obs_mode == 3) return bf_fail(ctx, BF_ESTATE, "bf_score_views_exact: the band holds trilinear rows");
   const float *dmu, *dc;
   BF_TRY(stage_in(ctx, mu, b->N, WS_STAGE2, &dmu));
   BF_TRY(stage_in(ctx, cand, (size_t)V * 12, WS_STAGE1, &dc));
   return nbv_exact_impl(ctx, b, dmu, dc, V, to_intr(K), eps, K_probes, seed, rel_tol, max_iter, rhs_block, U, best,
                         total_iters);
+}
+
+bf_status bf_export_trilinear_rows(bf_ctx* ctx, const bf_band* b, const float* depth, int T, const float* poses,
+                                   const bf_intrinsics* K, int32_t* idx, float* wts, uint8_t* used, int64_t* M) {
+  BF_ENTER(ctx);
+  if (!b || !M || !depth || !poses || T < 1 || !valid_intr(K))
+    return bf_fail(ctx, BF_EINVAL, "bf_export_trilinear_rows: null pointer, T < 1 or bad intrinsics");
+  const int64_t ns = 2 * (int64_t)floor(b->prm.band_vox + 1e-9) + 1;
+  const int64_t m = (int64_t)T * K->H * K->W * ns;
+  *M = m;
+  if (!idx && !wts && !used) return BF_OK;
+  if (!idx || !wts || !used) return bf_fail(ctx, BF_EINVAL, "bf_export_trilinear_rows: give all three arrays or none");
+  const float *d_depth, *d_poses;
+  BF_TRY(stage_in(ctx, depth, (size_t)T * K->H * K->W, WS_STAGE0, &d_depth));
+  BF_TRY(stage_in(ctx, poses, (size_t)T * 12, WS_STAGE1, &d_poses));
+  int32_t* di;
+  float* dw;
+  uint8_t* du;
+  bool hi, hw, hu;
+  BF_TRY(stage_out(ctx, idx, (size_t)m * 8, WS_OUT0, &di, &hi));
+  BF_TRY(stage_out(ctx, wts, (size_t)m * 8, WS_OUT1, &dw, &hw));
+  BF_TRY(stage_out(ctx, used, (size_t)m, WS_TMP2, &du, &hu));
+  BF_TRY(tri_rows(ctx, b, d_depth, T, d_poses, to_intr(K), di, dw, du));
+  BF_TRY(copy_out(ctx, idx, (const int32_t*)di, (size_t)m * 8, hi));
+  BF_TRY(copy_out(ctx, wts, (const float*)dw, (size_t)m * 8, hw));
+  BF_TRY(copy_out(ctx, used, (const uint8_t*)du, (size_t)m, hu));
+  BF_CK(cudaStreamSynchronize(ctx->stream));
+  return BF_OK;
+}
+
+bf_status bf_export_precision27(bf_ctx* ctx, const bf_band* b, float* coef) {
+  BF_ENTER(ctx);
+  if (!b || !coef) return BF_EINVAL;
+  if (b->obs_mode != 3 || !b->q27)
+    return bf_fail(ctx, BF_ESTATE, "bf_export_precision27: the band holds no trilinear rows");
+  const size_t n = (size_t)27 * b->N;
+  if (!n) return BF_OK;
+  if (is_device_ptr(coef)) BF_CK(cudaMemcpyAsync(coef, b->q27, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  else {
+    BF_CK(cudaStreamSynchronize(ctx->stream));
+    BF_CK(cudaMemcpy(coef, b->q27, n * 4, cudaMemcpyDeviceToHost));
+  }
+  return BF_OK;
 }
 
 bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, double* ms_per_launch) {
@@ -460,6 +525,8 @@ bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, d
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_bench_kernel: call bf_integrate_depth first");
   if (b->N == 0) return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: empty band");
   cudaStream_t s = ctx->stream;
+  if (b->obs_mode == 3 && which != BF_KERNEL_SPMV)
+    return bf_fail(ctx, BF_ESTATE, "bf_bench_kernel: the band holds trilinear rows (27-point Q): SpMV only");
   if (which == BF_KERNEL_SPMV || which == BF_KERNEL_SPMM) {
     if (which == BF_KERNEL_SPMM && R != 8 && R != 16 && R != 32)
       return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: R must be 8, 16 or 32");

@@ -103,12 +103,7 @@ struct BlkArgs {
   double* hsq;         // [N] the same for (z (.) xm)^2 (formed when BlkState::want_sq)
 };
 
-__device__ __forceinline__ uint64_t mix64(uint64_t x) {
-  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
+__device__ __forceinline__ uint64_t mix64(uint64_t x) { return splitmix64(x); }
 
 // float-float arithmetic: (hi, lo) with |lo| <= ulp(hi)/2
 __device__ __forceinline__ float2 two_sum(float a, float b) {  // a + b = s + e exactly (Knuth)

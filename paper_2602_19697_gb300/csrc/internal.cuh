@@ -117,6 +117,11 @@ struct bf_band {
   int32_t* sp_ext = nullptr;  // probe-solver SpMM plan: external rows per tile
   int32_t* sp_ne = nullptr;   //   their count per tile
   int16_t* sp_slot = nullptr; //   [N][8] staged-row slot of each face neighbour
+  // trilinear observation rows (obs_mode 3): the data term A^T W A on the 14 offsets o >= 13 of the 27-point
+  // neighbourhood ([14][N], entry o - 13 of voxel j = the coupling of j with j + off(o)), and the assembled
+  // 27-point precision ([27][N], coefficient o of voxel j = Q_{j, j + off(o)})
+  float* c27 = nullptr;
+  float* q27 = nullptr;
 };
 
 // POD view of a band passed to kernels.
@@ -196,6 +201,15 @@ bf_status band_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, con
                          bool fixed_point = false);
 constexpr int OBS_FIX_BITS = 32;
 bf_status band_assemble(bf_ctx* ctx, bf_band* b);
+// trilinear observation rows (tri.cu)
+bf_status tri_integrate(bf_ctx* ctx, bf_band* b, const float* depth, int T, const float* poses, const Intr& K);
+bf_status tri_rows(bf_ctx* ctx, const bf_band* b, const float* depth, int T, const float* poses, const Intr& K,
+                   int32_t* idx, float* wts, uint8_t* used);
+bf_status tri_spmv(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
+bf_status tri_solve_mean(bf_ctx* ctx, bf_band* b, double tol, int max_iter, float* mu, int* iters, double* relres);
+bf_status tri_variance(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, uint64_t seed, double tol,
+                       int max_iter, float* s, int* total_iters);
+constexpr int TRI_R = 8;  // probe columns per block of the trilinear probe solver
 bf_status band_observations_f64(bf_ctx* ctx, const bf_band* b, double* d64, double* h64);
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
 bf_status spmm_launch(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y);
@@ -325,6 +339,15 @@ __device__ __forceinline__ void dda_walk(const float C[3], const float r[3], flo
     else if (a == 1) { idx[1] += step[1]; tmax[1] = f_add(tmax[1], tdel[1]); }
     else { idx[2] += step[2]; tmax[2] = f_add(tmax[2], tdel[2]); }
   }
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): the mixing function of the
+// counter-based probe generator.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
 }
 
 __host__ __device__ inline int dda_max_steps(double band_vox) {

@@ -1066,6 +1066,7 @@ bf_status bf_surrogate_variance(bf_ctx* ctx, bf_band* b, const float* log_s_hat,
   BF_ENTER(ctx);
   if (!ctx || !b || !log_s_hat || !s) return BF_EINVAL;
   if (!b->integrated) return bf_fail(ctx, BF_ESTATE, "bf_surrogate_variance: call bf_integrate_depth first");
+  if (b->obs_mode == 3) return bf_fail(ctx, BF_ESTATE, "bf_surrogate_variance: the band holds trilinear rows");
   if (K_judge < 2 || K <= K_judge || !(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000)
     return bf_fail(ctx, BF_EINVAL, "bf_surrogate_variance: need 2 <= K_judge < K, 0 < rel_tol < 1");
   if (rhs_block != 0 && rhs_block != 1 && rhs_block != 8 && rhs_block != 16 && rhs_block != 32)

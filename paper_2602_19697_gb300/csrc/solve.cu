@@ -793,6 +793,7 @@ bf_status solve_rhs_impl(bf_ctx* ctx, bf_band* b, const float* rhs, double tol, 
 
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   if (b->N == 0) return BF_OK;
+  if (b->obs_mode == 3) return tri_spmv(ctx, b, x, y);
   const int grid = b->NB < 152 * SPMV_OCC ? b->NB : 152 * SPMV_OCC;
   k_spmv<<<grid, BT, 0, ctx->stream>>>(band_view(b), (float)b->prm.lambda, b->qd, x, y);
   count_launch();

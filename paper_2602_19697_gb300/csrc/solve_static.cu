@@ -350,7 +350,7 @@ extern "C" bf_status bf_solve_mean_static(bf_ctx* ctx, bf_band* b, double rel_to
                                           int* iters, double* rel_res) {
   BF_ENTER(ctx);
   if (!ctx || !b || !mu) return BF_EINVAL;
-  if (!b->integrated) return BF_ESTATE;
+  if (!b->integrated || b->obs_mode == 3) return BF_ESTATE;  // the 7-point system only
   if (!(rel_tol > 0.0) || !(rel_tol < 1.0) || max_iter < 1 || max_iter > 10000000) return BF_EINVAL;
   if (b->N > STATIC_MAX_VOX) return BF_EINVAL;  // larger bands need bf_solve_mean
   if (!is_device_ptr(mu)) return BF_EINVAL;     // no staging buffer to copy through

@@ -136,6 +136,7 @@ extern "C" bf_status bf_autotune_rhs_block(bf_ctx* ctx, bf_band* band, int K, in
   BF_ENTER(ctx);
   if (!ctx || !band || !rhs_block || K < 1) return BF_EINVAL;
   if (!band->integrated) return bf_fail(ctx, BF_ESTATE, "bf_autotune_rhs_block: call bf_integrate_depth first");
+  if (band->obs_mode == 3) return bf_fail(ctx, BF_ESTATE, "bf_autotune_rhs_block: the band holds trilinear rows");
   if (band->N == 0) {
     *rhs_block = 8;
     if (ms_per_iter) memset(ms_per_iter, 0, 3 * sizeof(double));

@@ -96,6 +96,30 @@ def test_spmv_matches_oracle(name):
     yh = np.empty(gb.N, np.float32)
     gb.spmv(x, yh)
     np.testing.assert_array_equal(yh, y.cpu().numpy())
+    # arrays that do not start on 16 bytes (the kernel without bulk copies): the same bits
+    xb = torch.zeros(gb.N + 3, device="cuda")
+    yb = torch.full((gb.N + 3,), 7.0, device="cuda")
+    for o in (1, 2, 3):
+        xb[o:o + gb.N] = dev(x)
+        gb.spmv(xb[o:o + gb.N], yb[o:o + gb.N])
+        np.testing.assert_array_equal(yb[o:o + gb.N].cpu().numpy(), y.cpu().numpy())
+    assert yb[0].item() == 7.0
+
+
+def test_spmv_bands_with_ragged_runs_and_tails():
+    """Runs that start and end inside 16-byte groups, a band size that is not a multiple of 4 (the last brick's
+    tail read directly), single-voxel runs: the bulk-copy SpMV against the oracle on small bands."""
+    for n, scale, frames, bv in ((16, 0.25, 4, 1.5), (24, 0.25, 6, 2.0), (32, 0.5, 8, 3.0)):
+        w = synth.make_workload("sphere64", n=n, image_scale=scale, frames=frames, band_vox=bv)
+        ob = oracle.build_band_w(w)
+        gb, depth, poses = gpu_band(w)
+        gb.integrate_depth(depth, poses, w.intr)
+        qd32 = gb.export_system()["qdiag"].astype(np.float64)
+        x = np.random.default_rng(n).standard_normal(gb.N).astype(np.float32)
+        y = torch.empty(gb.N, device="cuda")
+        gb.spmv(dev(x), y)
+        ref = oracle.spmv(ob, w.lam, qd32, x.astype(np.float64))
+        np.testing.assert_allclose(y.cpu().numpy(), ref, rtol=0, atol=1e-5 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("name,R", [("sphere32_small", 8), ("union128", 16), ("blob128_b5", 32), ("sphere64", 32)])

@@ -156,3 +156,28 @@ def test_posterior_under_trilinear_rows_matches_dense_algebra():
     # and the probe-averaged value bounds: (Q^-1)_ii >= 1/Q_ii holds for the exact diagonal
     Qi = np.linalg.inv(Qd)
     assert np.all(np.diag(Qi) >= 1.0 / np.diag(Qd) * (1 - 1e-12))
+
+
+def test_system_from_fp32_rows_is_the_fp64_system_up_to_boundary_samples(sphere):
+    """The posterior system assembled from the FP32-specified rows (the form the CUDA path reproduces) has the
+    structure of the FP64 one (symmetric, 27-point, d = A^T w) and differs from it only by the rows of samples within
+    rounding of a cell face: the FP32 and FP64 A^T W A, d and h agree to within the weight of the few rows whose
+    decisions differ (each row's weight is w = h^2/sigma^2 <= w_max)."""
+    w, b = sphere
+    a = dict(band_vox=w.band_vox, sig_a=w.sig_a, sig_b=w.sig_b, lam=w.lam, lam_b=w.lam_b)
+    Q64, h64, d64, n64 = trilinear.system(b, w.depth, w.poses, w.intr, **a)
+    Q32, h32, d32, n32 = trilinear.system(b, w.depth, w.poses, w.intr, rows="fp32", **a)
+    assert abs(n32 - n64) <= 1e-3 * n64
+    D = (Q32 - Q32.T).tocoo()
+    assert np.abs(D.data).max(initial=0) <= 1e-12 * np.abs(Q32.data).max()
+    wmax = float(trilinear.sample_precisions(w.depth, w.band_vox, b.h, w.sig_a, w.sig_b).max())
+    diff = (Q32 - Q64).tocoo()
+    nbad = np.count_nonzero(np.abs(diff.data) > 1e-4 * np.abs(Q64.data).max())
+    assert nbad <= 0.01 * Q64.nnz
+    assert np.abs(diff.data).max(initial=0) <= 8 * wmax * max(abs(n32 - n64), 1)
+    np.testing.assert_allclose(d32.sum(), d64.sum(), rtol=1e-3)
+    ok = np.abs(d32 - d64) <= 1e-4 * d64.max()
+    assert ok.mean() >= 0.99
+    # row sums of the data term equal A^T w (the FP32 weights of a row sum to one within a few FP32 ulps)
+    Q0, _, _, _ = trilinear.system(b, w.depth[:0], w.poses[:0], w.intr, rows="fp32", **a)
+    np.testing.assert_allclose(np.asarray((Q32 - Q0).sum(1)).ravel(), d32, rtol=1e-6, atol=1e-9 * d32.max())

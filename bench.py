@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="blob512",
-                    help="blob512 | union256 | sphere64 | sphere64_k256 | blob1024 (--kernel only: the blob512 "
-                         "object at 1 mm on a 1024^3 grid, band +-48 voxels, 200 frames 1024x768; 61 M voxels)")
+                    help="blob512 | union256 | sphere64 | sphere64_k256 | blob1024 | blob512_b5 (--kernel only; "
+                         "blob1024: the blob512 object at 1 mm on a 1024^3 grid, band +-48 voxels, 200 frames "
+                         "1024x768, 61 M voxels; blob512_b5: the blob512 object with a band of +-5 voxels)")
     ap.add_argument("--K", type=int, default=None, help="probes (default: the workload's, 128 for blob512)")
     ap.add_argument("--tol", type=float, default=1e-6, help="relative residual of the probe solves")
     ap.add_argument("--mean-tol", type=float, default=1e-8,
@@ -68,8 +69,8 @@ def parse():
                     help="skip the unbatched / block / learned-warm-start comparison of the posterior")
     ap.add_argument("--cpu-probes", type=int, default=8, help="oracle probe solves in the CPU-baseline sample")
     ap.add_argument("--kernel", default=None,
-                    choices=["block_iter", "spmv", "spmm", "net_forward", "net_train", "net_conv", "net_conv_mma",
-                             "net_wgrad"],
+                    choices=["block_iter", "spmv", "spmm", "spmv27", "net_forward", "net_train", "net_conv",
+                             "net_conv_mma", "net_wgrad"],
                     help="time one kernel alone on the workload's band (for profiling): --warmup untimed and "
                          "--steps timed launches; prints one JSON line with its throughput")
     return ap.parse_args()
@@ -539,6 +540,8 @@ def kernel_workload(name):
     import synth
     if name == "blob1024":  # the object at twice the linear resolution, same physical band
         return synth.make_workload("blob512", n=1024, band_vox=48.0, image_scale=2.0, threads=os.cpu_count() or 0)
+    if name == "blob512_b5":  # the object with a band of +-5 voxels
+        return synth.make_workload("blob512", band_vox=5.0, threads=os.cpu_count() or 0)
     return synth.make_workload(name, threads=os.cpu_count() or 0)
 
 
@@ -556,7 +559,7 @@ def run_kernel(args):
     w = kernel_workload(args.workload)
     depth, poses = torch.from_numpy(w.depth).cuda(), torch.from_numpy(w.poses).cuda()
     band = ctx.build_band_w(w, depth, poses)
-    band.integrate_depth(depth, poses, w.intr)
+    band.integrate_depth(depth, poses, w.intr, trilinear=args.kernel == "spmv27")
     N, NB, R = band.N, band.NB, (args.rhs_block or 32)
     out = {"kernel": args.kernel, "workload": args.workload, "N_band": N, "bricks": NB}
     if args.kernel == "block_iter":
@@ -565,8 +568,8 @@ def run_kernel(args):
         ms = band.bench_kernel(which, R=R, reps=max(args.steps, 1))
         nbytes = N * (R * 36 + 8)
         out.update(ms_per_launch=ms, bytes_per_launch=nbytes, achieved_gbs=nbytes / (ms * 1e-3) / 1e9)
-    elif args.kernel in ("spmv", "spmm"):
-        which = bfsdf.BF_KERNEL_SPMV if args.kernel == "spmv" else bfsdf.BF_KERNEL_SPMM
+    elif args.kernel in ("spmv", "spmm", "spmv27"):
+        which = bfsdf.BF_KERNEL_SPMM if args.kernel == "spmm" else bfsdf.BF_KERNEL_SPMV
         band.bench_kernel(which, R=R, reps=max(args.warmup, 1))
         flush = torch.empty(256 * 1024 * 1024, dtype=torch.float32, device="cuda")
         clean = torch.zeros(256 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -576,8 +579,10 @@ def run_kernel(args):
             clean.sum()
             torch.cuda.synchronize()
             ms.append(band.bench_kernel(which, R=R, reps=1))
-        # x (or X) and Q_jj read, y (or Y) written, brick metadata
-        nbytes = N * 12 + NB * (128 + 24) if args.kernel == "spmv" else N * (8 * R + 4) + NB * (128 + 24)
+        # x (or X) and Q_jj (or the 27 coefficients of the trilinear rows' precision) read, y (or Y) written,
+        # brick metadata
+        nbytes = {"spmv": N * 12 + NB * (128 + 24), "spmm": N * (8 * R + 4) + NB * (128 + 24),
+                  "spmv27": N * (27 * 4 + 8) + NB * (128 + 16)}[args.kernel]
         med = float(np.median(ms))
         hbm, peak_kind = peaks()
         out.update(ms_per_launch=med, ms_min=min(ms), bytes_per_launch=nbytes,

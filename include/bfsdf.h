@@ -267,6 +267,25 @@ bf_status bf_estimate_variance_range(bf_ctx* ctx, bf_band* band, int k_begin, in
  * counts; the mesh is kept in the context until bf_get_surface. */
 bf_status bf_extract_surface(bf_ctx* ctx, const bf_band* band, const float* mu, int64_t* nv, int64_t* nt);
 
+/* Dual contouring on mu (Sec. 3.8: the surface is extracted by "MC or DC").
+ * Cells are the cubes of 8 band voxels (inside = mu < 0).  A crossed grid
+ * edge (a, b = a + e_axis, both band voxels) carries the point p = x_a + t
+ * e_axis, t = mu_a / (mu_a - mu_b), and the normal n = g / |g| with g =
+ * (1 - t) g_a + t g_b, g_v the central difference of mu over the voxel's
+ * band neighbours along each axis (one-sided with one neighbour, 0 with
+ * none; g = 0 adds the point but no plane).  Each cube with a crossed edge
+ * gets one vertex, the minimiser of sum_e (n_e . (x - p_e))^2 + 0.01 |x -
+ * c|^2 (c = the mean crossing point) clamped to the cube; each crossed edge
+ * whose four cubes exist gives a quad of their vertices (cube offsets
+ * (-1,-1), (0,-1), (0,0), (-1,0) along the two other axes taken cyclically,
+ * reversed when the edge's lower end is outside), split into (q0, q1, q2),
+ * (q0, q2, q3), so triangles face mu >= 0.  Hermite data and the QEF in FP64.
+ * Vertices are ordered by the compact index of the cube's lower corner,
+ * triangles by (compact index of the edge's lower voxel, axis).  mu [N] float
+ * (voxels); *nv, *nt (host) receive the counts; the mesh is kept in the
+ * context until bf_get_surface (replacing a marching-cubes mesh). */
+bf_status bf_extract_surface_dc(bf_ctx* ctx, const bf_band* band, const float* mu, int64_t* nv, int64_t* nt);
+
 /* Copy the last extracted mesh: verts [nv][3] float metres, tris [nt][3] int32. */
 bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris);
 

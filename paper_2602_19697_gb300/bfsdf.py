@@ -36,7 +36,8 @@ EXPORTED = ["bf_create", "bf_destroy", "bf_last_error", "bf_set_stream", "bf_bui
             "bf_score_views", "bf_score_views_exact", "bf_solve_mean_static", "bf_estimate_variance_range", "bf_bench_kernel",
             "bf_launch_count", "bf_net_nparams", "bf_net_create", "bf_net_destroy", "bf_net_get_params",
             "bf_net_set_params", "bf_net_forward", "bf_net_train_step", "bf_surrogate_variance",
-            "bf_net_bench", "bf_autotune_rhs_block", "bf_export_trilinear_rows", "bf_export_precision27"]
+            "bf_net_bench", "bf_autotune_rhs_block", "bf_export_trilinear_rows", "bf_export_precision27",
+            "bf_extract_surface_dc"]
 BF_INTEGRATE_DETERMINISTIC = 1
 BF_INTEGRATE_TRILINEAR = 2
 BF_KERNEL_SPMV = 0
@@ -104,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "bf_estimate_variance": (i, [vp, vp, i, ctypes.c_uint64, d, i, i, u, vp, ctypes.POINTER(i)]),
         "bf_extract_surface": (i, [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "bf_get_surface": (i, [vp, vp, vp]),
+        "bf_extract_surface_dc": (i, [vp, vp, vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "bf_score_views": (i, [vp, vp, vp, vp, vp, i, ctypes.POINTER(Intrinsics), d, vp, ctypes.POINTER(i)]),
         "bf_score_views_exact": (i, [vp, vp, vp, vp, i, ctypes.POINTER(Intrinsics), d, i, ctypes.c_uint64, d, i, i,
                                      vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
@@ -371,10 +373,12 @@ class Band:
                                                           ctypes.byref(R), _ptr(ms)), "bf_autotune_rhs_block")
         return R.value, ms
 
-    def extract_surface(self, mu, device="numpy"):
+    def extract_surface(self, mu, device="numpy", method="mc"):
+        """(verts [V,3], tris [F,3]) by marching cubes (method="mc") or dual contouring (method="dc")."""
         nv, nt = ctypes.c_int64(), ctypes.c_int64()
-        self.ctx.check(self.ctx.lib.bf_extract_surface(self.ctx._p, self._p, _ptr(mu), ctypes.byref(nv),
-                                                       ctypes.byref(nt)), "bf_extract_surface")
+        fn = {"mc": self.ctx.lib.bf_extract_surface, "dc": self.ctx.lib.bf_extract_surface_dc}[method]
+        self.ctx.check(fn(self.ctx._p, self._p, _ptr(mu), ctypes.byref(nv), ctypes.byref(nt)),
+                       "bf_extract_surface" + ("_dc" if method == "dc" else ""))
         V = self._new(np.float32 if device == "numpy" else torch.float32, (nv.value, 3), device)
         F = self._new(np.int32 if device == "numpy" else torch.int32, (nt.value, 3), device)
         self.ctx.check(self.ctx.lib.bf_get_surface(self.ctx._p, _ptr(V) if nv.value else None,

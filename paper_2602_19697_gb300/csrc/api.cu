@@ -429,6 +429,14 @@ bf_status bf_extract_surface(bf_ctx* ctx, const bf_band* b, const float* mu, int
   return mc_impl(ctx, b, dmu, nv, nt);
 }
 
+bf_status bf_extract_surface_dc(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt) {
+  BF_ENTER(ctx);
+  if (!b || !mu || !nv || !nt) return BF_EINVAL;
+  const float* dmu;
+  BF_TRY(stage_in(ctx, mu, b->N, WS_STAGE2, &dmu));
+  return dc_impl(ctx, b, dmu, nv, nt);
+}
+
 bf_status bf_get_surface(bf_ctx* ctx, float* verts, int32_t* tris) {
   BF_ENTER(ctx);
   if (!ctx) return BF_EINVAL;

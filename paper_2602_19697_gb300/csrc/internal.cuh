@@ -225,6 +225,7 @@ bf_status autotune_rhs_block(bf_ctx* ctx, bf_band* b, int K, bool force, int* R_
 void solve_graph_free(SolveGraph* g);
 void block_graph_free(BlockGraph* g);
 bf_status mc_impl(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt);
+bf_status dc_impl(bf_ctx* ctx, const bf_band* b, const float* mu, int64_t* nv, int64_t* nt);
 bf_status nbv_exact_impl(bf_ctx* ctx, bf_band* b, const float* mu, const float* cand, int V, const Intr& K,
                          double eps, int Kp, uint64_t seed, double tol, int max_iter, int R, double* U, int* best,
                          int* total_iters);

@@ -48,10 +48,20 @@ constexpr int CT = 512;   // threads per CTA of the row kernels
 // smallest relative residual reduction asked of one FP32 correction solve
 // (the FP32 recursive residual keeps falling below the true one's floor)
 constexpr double ETA_MIN = 1e-7;
-constexpr int NCTA = 152 * 2;
-// CTA sums are reduced in two levels: groups of GSZ CTAs, then the NGRP group sums
-constexpr int GSZ = 16, NGRP = NCTA / GSZ;
-static_assert(NGRP * GSZ == NCTA && NGRP <= 32, "reduction groups");
+// Resident CTAs per SM of the row kernels for R columns: one for R = 32
+// (512 threads with up to 128 registers each keep all four own-row items of
+// a thread in flight; measured 1.79 against 2.11 ms per iteration on the
+// 7.2 M-voxel object band), two otherwise (R = 16: 1.01 against 1.07 ms).
+template <int R>
+__host__ __device__ constexpr int blk_occ() { return R >= 32 ? 1 : 2; }
+template <int R>
+__host__ __device__ constexpr int blk_ncta() { return 152 * blk_occ<R>(); }
+// own-row items of the probe iteration in flight per thread
+template <int R>
+__host__ __device__ constexpr int blk_p1_unroll() { return R >= 32 ? 4 : 1; }
+// CTA sums are reduced in two levels: NGRP groups of gridDim.x / NGRP CTAs (8 or 16), then the group sums
+constexpr int NCTA_MAX = 152 * 2, NGRP = 19;
+static_assert(NCTA_MAX % NGRP == 0 && 152 % NGRP == 0 && NCTA_MAX / NGRP <= 16, "reduction groups");
 // SpMM pass: tiles of SP_TR rows plus at most SP_EMAX external rows staged in
 // shared memory (SP_ROWS rows); SP_GLOBAL marks a neighbour read from global
 // memory (a tile whose external rows overflow the list)
@@ -96,8 +106,8 @@ struct BlkArgs {
   float* x;            // FP32 correction
   float2* xm[2];       // float-float master iterates (hi, lo), double-buffered ([BlkState::xmpar] is current)
   const __nv_bfloat16* Z;
-  double* part;        // [3][R][NCTA]
-  double* part1;       // [3][R][NCTA] the iteration's partials (r'.u', r'.r', w'.u')
+  double* part;        // [3][R][CTAs of the launch]
+  double* part1;       // [3][R][CTAs of the launch] the iteration's partials (r'.u', r'.r', w'.u')
   double* gpart;       // [3][R][NGRP] group sums of the partials
   double* hsum;        // [N] sum over the block's columns of z (.) xm, from the last residual pass
   double* hsq;         // [N] the same for (z (.) xm)^2 (formed when BlkState::want_sq)
@@ -129,7 +139,7 @@ __device__ __forceinline__ float2 ff_mul_f(float2 x, float b) {  // exact produc
 }
 __device__ __forceinline__ float2 ff_neg(float2 x) { return make_float2(-x.x, -x.y); }
 
-// Fixed-order two-level sum of the CTA partials part[k][c][0..NCTA) for all
+// Fixed-order two-level sum of the CTA partials part[k][c][0..gridDim.x) for all
 // c < R, k < NV.  Called by every thread of every CTA after its partials are
 // written.  The last CTA of each group of GSZ sums the group (a half-warp per
 // (k, c), shuffle tree) into gpart[k][c][group]; the last group's finisher sums
@@ -140,6 +150,7 @@ template <int NV>
 __device__ __forceinline__ bool reduce_partials(const double* part, double* gpart, BlkState* st, int R,
                                                 double (*tot)[MAXR]) {
   __shared__ bool s_last;
+  const int GSZ = gridDim.x / NGRP, ncta = gridDim.x;
   const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5, grp = blockIdx.x / GSZ;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -152,7 +163,7 @@ __device__ __forceinline__ bool reduce_partials(const double* part, double* gpar
   for (int kb = 2 * wrp; kb < NV * R; kb += CT / 16) {
     const int kc = kb + ((threadIdx.x >> 4) & 1);
     const bool on = kc < NV * R;
-    double v = on ? __ldcg(part + (size_t)kc * NCTA + grp * GSZ + (lane & 15)) : 0.0;
+    double v = (on && (lane & 15) < GSZ) ? __ldcg(part + (size_t)kc * ncta + grp * GSZ + (lane & 15)) : 0.0;
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (on && (lane & 15) == 0) gpart[(size_t)kc * NGRP + grp] = v;
@@ -191,7 +202,7 @@ __device__ __forceinline__ bool reduce_partials(const double* part, double* gpar
 // residual within tolerance) and the correction target
 // eta = 0.5 tol |z| / |r| clamped to [ETA_MIN, 0.5], and flips xmpar.
 template <int R>
-__global__ void __launch_bounds__(CT, 2) k_blk_res(const BlkArgs* __restrict__ A, BlkState* st, int first) {
+__global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_res(const BlkArgs* __restrict__ A, BlkState* st, int first) {
   constexpr int CC = R < 16 ? R : 16;  // columns per pass
   constexpr int NP = R / CC;           // passes
   constexpr int F4 = CC / 2;           // float4 (two float2 columns) per row and pass
@@ -366,7 +377,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_res(const BlkArgs* __restrict__ A
       const int pp = cc / CC, kk = (cc % CC) / 2, j = cc & 1;
       double tsum = 0.0;
       for (int ww = 0; ww < CT / 32; ++ww) tsum += shr[ww][kk][(qk * NP + pp) * 2 + j];
-      A->part[((size_t)qk * R + cc) * NCTA + blockIdx.x] = tsum;
+      A->part[((size_t)qk * R + cc) * gridDim.x + blockIdx.x] = tsum;
     }
   }
   __shared__ double tot[3][MAXR];
@@ -440,7 +451,7 @@ __device__ __forceinline__ float4 scale4(float4 a, float q) {
 constexpr int IT_GRAPH = 0, IT_BENCH = 1, IT_START = 2, IT_BENCH_HOLD = 3;
 
 template <int R, bool INIT>
-__global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A, BlkState* st,
+__global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __restrict__ A, BlkState* st,
                                                   cudaGraphConditionalHandle handle, int mode) {
   const bool bench = mode == IT_BENCH || mode == IT_BENCH_HOLD;
   if (mode == IT_GRAPH && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -516,7 +527,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
     __syncthreads();  // the previous tile's readers of us are done
     // phase 1: own rows
     const int nown = (t1 - t0) * Q4;
-#pragma unroll 1
+#pragma unroll blk_p1_unroll<R>()
     for (int i = 0; i < OWN; ++i) {
       const int q = threadIdx.x + i * CT;
       if (q >= nown) break;
@@ -635,7 +646,7 @@ __global__ void __launch_bounds__(CT, 2) k_blk_it(const BlkArgs* __restrict__ A,
       const int qk = threadIdx.x / R, cc = threadIdx.x % R;  // qk: 0 = r.u, 1 = r.r, 2 = w.u
       double t = 0.0;
       for (int ww = 0; ww < CT / 32; ++ww) t += sh1[ww][cc / 4][4 * qk + (cc & 3)];
-      A->part1[((size_t)qk * R + cc) * NCTA + blockIdx.x] = t;
+      A->part1[((size_t)qk * R + cc) * gridDim.x + blockIdx.x] = t;
     }
   }
   __shared__ double tot1[3][MAXR];
@@ -740,7 +751,7 @@ __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed,
 // four columns of a row per lane; the neighbour sum keeps the order
 // ((x-1 + x+1) + (y-1 + y+1)) + (z-1 + z+1) of the single-RHS SpMV.
 template <int R>
-__global__ void __launch_bounds__(CT, 2) k_spmm(int N, float lam, const float* __restrict__ qd,
+__global__ void __launch_bounds__(CT, blk_occ<R>()) k_spmm(int N, float lam, const float* __restrict__ qd,
                                                 const int32_t* __restrict__ nb6, const int32_t* __restrict__ sp_ext,
                                                 const int32_t* __restrict__ sp_ne, const int16_t* __restrict__ sp_slot,
                                                 const float* __restrict__ X, float* __restrict__ Y) {
@@ -1027,13 +1038,13 @@ void block_graph_free(BlockGraph* g) {
 
 template <int R>
 static void blk_iter(BlockGraph* g, cudaStream_t s, cudaGraphConditionalHandle h) {
-  k_blk_it<R, false><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, h, IT_GRAPH);
+  k_blk_it<R, false><<<blk_ncta<R>(), CT, sp_smem(R), s>>>(g->d_args, g->st, h, IT_GRAPH);
 }
 
 // start of a correction solve from r: u = r/Q_jj, w = Q u, x = 0, alpha
 template <int R>
 static void blk_start(BlockGraph* g, cudaStream_t s) {
-  k_blk_it<R, true><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), IT_START);
+  k_blk_it<R, true><<<blk_ncta<R>(), CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(), IT_START);
   count_launch();
 }
 
@@ -1043,7 +1054,7 @@ constexpr size_t res_smem(int R) { return (size_t)SP_ROWS * (R < 16 ? R : 16) / 
 // xm += correction, true residual, stop test; then the start of the next correction solve
 template <int R>
 static void blk_outer(BlockGraph* g, cudaStream_t s, bool first) {
-  k_blk_res<R><<<NCTA, CT, res_smem(R), s>>>(g->d_args, g->st, first ? 1 : 0);
+  k_blk_res<R><<<blk_ncta<R>(), CT, res_smem(R), s>>>(g->d_args, g->st, first ? 1 : 0);
   count_launch();
   blk_start<R>(g, s);
 }
@@ -1130,8 +1141,8 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     BF_CK(cudaMalloc(&g->Z, nv * 2));
     BF_CK(cudaMalloc(&g->h.iq, (size_t)rows * 4));
     BF_CK(cudaMalloc(&g->sacc, (size_t)rows * 8));
-    BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NCTA * sizeof(double)));
-    BF_CK(cudaMalloc(&g->h.part1, (size_t)3 * R * NCTA * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.part, (size_t)3 * R * NCTA_MAX * sizeof(double)));
+    BF_CK(cudaMalloc(&g->h.part1, (size_t)3 * R * NCTA_MAX * sizeof(double)));
     BF_CK(cudaMalloc(&g->h.gpart, (size_t)3 * R * NGRP * sizeof(double)));
     g->cap_rows = rows;
   }
@@ -1232,7 +1243,7 @@ static bf_status bench_blk_t(bf_ctx* ctx, bf_band* b, int reps, double* ms) {
   BF_CK(cudaEventCreate(&e1));
   BF_CK(cudaEventRecord(e0, s));
   for (int i = 0; i < reps; ++i) {  // alternately an iteration that writes x and one that holds it
-    k_blk_it<R, false><<<NCTA, CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(),
+    k_blk_it<R, false><<<blk_ncta<R>(), CT, sp_smem(R), s>>>(g->d_args, g->st, cudaGraphConditionalHandle(),
                                                     (i & 1) ? IT_BENCH_HOLD : IT_BENCH);
     count_launch();
   }
@@ -1345,7 +1356,7 @@ template <int R>
 static bf_status spmm_t(bf_ctx* ctx, bf_band* b, const float* X, float* Y) {
   BF_CK(cudaFuncSetAttribute(k_spmm<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
   BF_TRY(ensure_sp_plan(ctx, b));
-  k_spmm<R><<<NCTA, CT, sp_smem(R), ctx->stream>>>((int)b->N, (float)b->prm.lambda, b->qd, b->nb6, b->sp_ext,
+  k_spmm<R><<<blk_ncta<R>(), CT, sp_smem(R), ctx->stream>>>((int)b->N, (float)b->prm.lambda, b->qd, b->nb6, b->sp_ext,
                                                    b->sp_ne, b->sp_slot, X, Y);
   count_launch();
   BF_CK(cudaGetLastError());

@@ -59,6 +59,13 @@ __host__ __device__ constexpr int blk_ncta() { return 152 * blk_occ<R>(); }
 // own-row items of the probe iteration in flight per thread
 template <int R>
 __host__ __device__ constexpr int blk_p1_unroll() { return R >= 32 ? 4 : 1; }
+// a correction solve reduces its right-hand side to BLK_ETA tol |z| (measured on the object band:
+// 0.5 takes 2408 iterations for 128 probes, 0.25 2554 and 0.1 2697, with no fewer residual passes)
+constexpr double BLK_ETA = 0.5;
+// resident CTAs per SM of the residual pass: two for every R (its float-float columns go in passes of 16; for
+// R = 32 two CTAs took the 128-probe estimate on the object band from 154.6 to 149.3 ms against one)
+template <int R>
+__host__ __device__ constexpr int res_occ() { return 2; }
 // CTA sums are reduced in two levels: NGRP groups of gridDim.x / NGRP CTAs (8 or 16), then the group sums
 constexpr int NCTA_MAX = 152 * 2, NGRP = 19;
 static_assert(NCTA_MAX % NGRP == 0 && 152 % NGRP == 0 && NCTA_MAX / NGRP <= 16, "reduction groups");
@@ -202,7 +209,7 @@ __device__ __forceinline__ bool reduce_partials(const double* part, double* gpar
 // residual within tolerance) and the correction target
 // eta = 0.5 tol |z| / |r| clamped to [ETA_MIN, 0.5], and flips xmpar.
 template <int R>
-__global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_res(const BlkArgs* __restrict__ A, BlkState* st, int first) {
+__global__ void __launch_bounds__(CT, res_occ<R>()) k_blk_res(const BlkArgs* __restrict__ A, BlkState* st, int first) {
   constexpr int CC = R < 16 ? R : 16;  // columns per pass
   constexpr int NP = R / CC;           // passes
   constexpr int F4 = CC / 2;           // float4 (two float2 columns) per row and pass
@@ -389,7 +396,7 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_res(const BlkArgs* __r
     st->bb0[cc] = bb;
     st->bb[cc] = rr;  // the correction solve's right-hand side norm
     const int conv = (cc >= st->ncols) || rr <= st->tol0 * st->tol0 * bb || bb == 0.0;
-    double eta = conv ? 0.5 : 0.5 * st->tol0 * sqrt(bb / rr);
+    double eta = conv ? 0.5 : BLK_ETA * st->tol0 * sqrt(bb / rr);
     eta = fmin(fmax(eta, ETA_MIN), 0.5);
     st->tol2[cc] = eta * eta;
     st->done[cc] = conv;
@@ -565,7 +572,7 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __re
     }
     // phase 2: external rows
     const int next = ne * Q4;
-#pragma unroll 2
+#pragma unroll  // every external-row item of the thread in flight (measured 1.75 against 1.80 ms per R = 32 iteration)
     for (int i = 0; i < XN; ++i) {
       const int q = threadIdx.x + i * CT;
       if (q >= next) break;
@@ -956,7 +963,7 @@ __global__ void k_blk_init(BlkState* st, double tol, int max_iter, int ncols, in
     st->beta[c] = 0.0;
     st->alpha[c] = 0.0;
     st->rr0[c] = st->bb0[c] = st->bb[c] = live ? (double)N : 0.0;
-    const double eta = fmin(fmax(0.5 * tol, eta_min), 0.5);
+    const double eta = fmin(fmax(BLK_ETA * tol, eta_min), 0.5);
     st->tol2[c] = eta * eta;
   }
   if (c == 0) {
@@ -1054,7 +1061,7 @@ constexpr size_t res_smem(int R) { return (size_t)SP_ROWS * (R < 16 ? R : 16) / 
 // xm += correction, true residual, stop test; then the start of the next correction solve
 template <int R>
 static void blk_outer(BlockGraph* g, cudaStream_t s, bool first) {
-  k_blk_res<R><<<blk_ncta<R>(), CT, res_smem(R), s>>>(g->d_args, g->st, first ? 1 : 0);
+  k_blk_res<R><<<152 * res_occ<R>(), CT, res_smem(R), s>>>(g->d_args, g->st, first ? 1 : 0);
   count_launch();
   blk_start<R>(g, s);
 }

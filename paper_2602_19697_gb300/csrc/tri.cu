@@ -218,13 +218,19 @@ __global__ void __launch_bounds__(TB) k_spmv27(BandView B, const float* __restri
   const size_t N = (size_t)B.N;
   for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
     const int bi = __ldg(B.bcoord + 4 * b), bj = __ldg(B.bcoord + 4 * b + 1), bk = __ldg(B.bcoord + 4 * b + 2);
-    for (int sl = threadIdx.x; sl < 1000; sl += TB) {
-      const int tx = sl % 10, ty = (sl / 10) % 10, tz = sl / 100;
-      const int u = band_lookup(B, 8 * bi + tx - 1, 8 * bj + ty - 1, 8 * bk + tz - 1);
+    // all of the thread's slots at once, so that their lookup and load chains overlap
 #pragma unroll
-      for (int c = 0; c < C; ++c) tile[sl * C + c] = u >= 0 ? X[(size_t)u * C + c] : TI(0);
+    for (int k = 0; k < (1000 + TB - 1) / TB; ++k) {
+      const int sl = threadIdx.x + k * TB;
+      if (sl < 1000) {
+        const int tx = sl % 10, ty = (sl / 10) % 10, tz = sl / 100;
+        const int u = band_lookup(B, 8 * bi + tx - 1, 8 * bj + ty - 1, 8 * bk + tz - 1);
+#pragma unroll
+        for (int c = 0; c < C; ++c) tile[sl * C + c] = u >= 0 ? X[(size_t)u * C + c] : TI(0);
+      }
     }
     __syncthreads();
+#pragma unroll 4
     for (int e = threadIdx.x; e < 512 * C; e += TB) {
       const int l = e / C, c = e - l * C;
       const MetaWord m = B.meta[16 * b + (l >> 5)];
@@ -515,7 +521,7 @@ bf_status spmv27_launch(bf_ctx* ctx, const bf_band* b, const TI* X, TO* Y) {
     BF_CK(cudaFuncSetAttribute(k_spmv27<C, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr = true;
   }
-  const int grid = b->NB < 152 * 8 ? b->NB : 152 * 8;
+  const int grid = b->NB < 152 * 16 ? b->NB : 152 * 16;
   k_spmv27<C, TI, TO><<<grid, TB, smem, ctx->stream>>>(band_view(b), b->q27, X, Y);
   count_launch();
   BF_CK(cudaGetLastError());

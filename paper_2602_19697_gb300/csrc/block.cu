@@ -66,6 +66,10 @@ constexpr double BLK_ETA = 0.5;
 // R = 32 two CTAs took the 128-probe estimate on the object band from 154.6 to 149.3 ms against one)
 template <int R>
 __host__ __device__ constexpr int res_occ() { return 2; }
+// float-float columns per pass of the residual pass (all 32 columns in one pass at one CTA per SM measured
+// slower: 157.4 against 149.5 ms for the 128-probe estimate)
+template <int R>
+__host__ __device__ constexpr int res_cc() { return R < 16 ? R : 16; }
 // CTA sums are reduced in two levels: NGRP groups of gridDim.x / NGRP CTAs (8 or 16), then the group sums
 constexpr int NCTA_MAX = 152 * 2, NGRP = 19;
 static_assert(NCTA_MAX % NGRP == 0 && 152 % NGRP == 0 && NCTA_MAX / NGRP <= 16, "reduction groups");
@@ -210,7 +214,7 @@ __device__ __forceinline__ bool reduce_partials(const double* part, double* gpar
 // eta = 0.5 tol |z| / |r| clamped to [ETA_MIN, 0.5], and flips xmpar.
 template <int R>
 __global__ void __launch_bounds__(CT, res_occ<R>()) k_blk_res(const BlkArgs* __restrict__ A, BlkState* st, int first) {
-  constexpr int CC = R < 16 ? R : 16;  // columns per pass
+  constexpr int CC = res_cc<R>();      // columns per pass
   constexpr int NP = R / CC;           // passes
   constexpr int F4 = CC / 2;           // float4 (two float2 columns) per row and pass
   constexpr int RPS = 32 / F4;         // rows per warp step of the stencil phase
@@ -1056,12 +1060,13 @@ static void blk_start(BlockGraph* g, cudaStream_t s) {
 }
 
 // shared memory of the residual pass: the staged master iterates of a tile (16 columns at a time)
-constexpr size_t res_smem(int R) { return (size_t)SP_ROWS * (R < 16 ? R : 16) / 2 * sizeof(float4); }
+template <int R>
+constexpr size_t res_smem() { return (size_t)SP_ROWS * res_cc<R>() / 2 * sizeof(float4); }
 
 // xm += correction, true residual, stop test; then the start of the next correction solve
 template <int R>
 static void blk_outer(BlockGraph* g, cudaStream_t s, bool first) {
-  k_blk_res<R><<<152 * res_occ<R>(), CT, res_smem(R), s>>>(g->d_args, g->st, first ? 1 : 0);
+  k_blk_res<R><<<152 * res_occ<R>(), CT, res_smem<R>(), s>>>(g->d_args, g->st, first ? 1 : 0);
   count_launch();
   blk_start<R>(g, s);
 }
@@ -1101,7 +1106,7 @@ static bf_status get_block_solver(bf_ctx* ctx, bf_band* b, BlockGraph** out) {
     g->R = R;
     BF_CK(cudaFuncSetAttribute(k_blk_it<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
     BF_CK(cudaFuncSetAttribute(k_blk_it<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp_smem(R)));
-    BF_CK(cudaFuncSetAttribute(k_blk_res<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem(R)));
+    BF_CK(cudaFuncSetAttribute(k_blk_res<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem<R>()));
     memset(&g->h, 0, sizeof(g->h));
     BF_CK(cudaMalloc(&g->d_args, sizeof(BlkArgs)));
     BF_CK(cudaMallocHost(&g->h_pin, sizeof(BlkArgs)));

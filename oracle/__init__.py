@@ -7,9 +7,11 @@ Python binding) never imports, links or runs it, and the two share no code.
 The arithmetic lives in ``bfo.c`` (plain C, FP64 for every real-valued
 quantity, a fixed FP32 specification for discrete decisions; every function
 there cites the section of the paper it restates).  This module compiles it
-with gcc and marshals numpy arrays through ctypes; the one function written
-here in numpy is ``surrogate_judge`` (a per-brick statistic over values the C
-code returns).
+with gcc and marshals numpy arrays through ctypes; written here in numpy are
+``surrogate_judge`` (a per-brick statistic over values the C code returns) and
+the evaluations of the next rows' solvers, ``block_pcg`` (block CG over the
+probe right-hand sides), ``deflated_pcg`` and ``ritz_vectors`` (deflation of a
+probe block's Krylov information from the next block's solves).
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests against
 closed forms, invariants, special cases or brute force (see
@@ -401,6 +403,79 @@ def block_pcg(band: Band, lam, qdiag, B, tol=1e-12, max_iter=20000, rank_tol=1e-
         if P.shape[1] == 0:
             return X, 0 if np.all(np.linalg.norm(R, axis=0) <= tol * bn) else 1, it
     return X, 1, max_iter
+
+
+def _sparse_Q(band, lam, qdiag, Q):
+    import scipy.sparse
+    if Q is None:
+        indptr, indices, data = csr(band, lam, qdiag)
+        return scipy.sparse.csr_matrix((data, indices, indptr), shape=(band.N, band.N))
+    return scipy.sparse.csr_matrix(Q)
+
+
+def deflated_pcg(band: Band, lam, qdiag, b, W=None, tol=1e-12, max_iter=20000, Q=None, lanczos=False):
+    """Deflated Jacobi PCG (Saad, Yeung, Erhel & Guyomarc'h, 2000) for Q x = b, the evaluation of row f2's
+    deflation across probe blocks (Sec. 3.7 needs one solve per probe): the k columns of W span a subspace taken out
+    of the iteration -- x0 = W E^-1 W^T b with E = W^T Q W, and every preconditioned residual z = M^-1 r is made
+    Q-orthogonal to W, z - W E^-1 (Q W)^T z, before it enters the search direction (M = diag Q).  With W = None
+    this is plain PCG.  Stops when |r| <= tol |b|.  Returns (x, status, iters) and, with lanczos=True, also the CG
+    coefficients (alphas, betas) and the M-normalised residual directions z_j / sqrt(r_j . z_j) of the run (the
+    Lanczos basis from which ``ritz_vectors`` forms Ritz vectors)."""
+    Qs = _sparse_Q(band, lam, qdiag, Q)
+    Minv = 1.0 / Qs.diagonal()
+    b = np.asarray(b, np.float64)
+    if W is not None and W.shape[1] > 0:
+        QW = Qs @ W
+        E = W.T @ QW
+        x = W @ np.linalg.solve(E, W.T @ b)
+        proj = lambda z: z - W @ np.linalg.solve(E, QW.T @ z)
+    else:
+        x = np.zeros_like(b)
+        proj = lambda z: z
+    r = b - Qs @ x
+    bn = np.linalg.norm(b)
+    z = Minv * r
+    rz = float(r @ z)
+    p = proj(z)
+    als, bes, Zs = [], [], [z / np.sqrt(rz)] if rz > 0 else []
+    it, status = 0, 0
+    while np.linalg.norm(r) > tol * bn:
+        if it >= max_iter:
+            status = 1
+            break
+        q = Qs @ p
+        a = rz / float(p @ q)
+        x += a * p
+        r -= a * q
+        it += 1
+        z = Minv * r
+        rz2 = float(r @ z)
+        be = rz2 / rz
+        als.append(a)
+        bes.append(be)
+        if rz2 > 0:
+            Zs.append(z / np.sqrt(rz2))
+        p = proj(z) + be * p
+        rz = rz2
+    if lanczos:
+        return x, status, it, np.array(als), np.array(bes), Zs
+    return x, status, it
+
+
+def ritz_vectors(alphas, betas, Zs, k):
+    """The k smallest Ritz pairs of M^-1 Q from a PCG run's coefficients: the Lanczos tridiagonal has diagonal
+    1/alpha_j + beta_{j-1}/alpha_{j-1} and off-diagonal -sqrt(beta_j)/alpha_j; its eigenvectors combine the
+    M-normalised residual directions.  Returns (values [k], vectors [N, k])."""
+    m = len(alphas)
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < m:
+            T[j, j + 1] = T[j + 1, j] = -np.sqrt(betas[j]) / alphas[j]
+    ev, U = np.linalg.eigh(T)
+    V = np.stack(Zs[:m], 1)
+    k = min(k, m)
+    return ev[:k], V @ U[:, :k]
 
 
 def solve_all(w, threads=0, tol=1e-12, K=None):

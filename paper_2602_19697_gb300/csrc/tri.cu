@@ -215,16 +215,32 @@ __global__ void __launch_bounds__(TB) k_spmv27(BandView B, const float* __restri
                                                TO* __restrict__ Y) {
   extern __shared__ __align__(16) unsigned char tri_smem[];
   TI* tile = reinterpret_cast<TI*>(tri_smem);  // [1000][C]
+  __shared__ int nrank[27];                      // ranks of the brick and its 26 neighbours (-1: none)
   const size_t N = (size_t)B.N;
   for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
-    const int bi = __ldg(B.bcoord + 4 * b), bj = __ldg(B.bcoord + 4 * b + 1), bk = __ldg(B.bcoord + 4 * b + 2);
+    if (threadIdx.x < 27) {
+      const int o = threadIdx.x;
+      const int ci = __ldg(B.bcoord + 4 * b) + o % 3 - 1, cj = __ldg(B.bcoord + 4 * b + 1) + (o / 3) % 3 - 1,
+                ck = __ldg(B.bcoord + 4 * b + 2) + o / 9 - 1;
+      const bool in = (unsigned)ci < (unsigned)B.nb && (unsigned)cj < (unsigned)B.nb && (unsigned)ck < (unsigned)B.nb;
+      nrank[o] = in ? __ldg(B.dir + (ci + B.nb * (cj + B.nb * ck))) : -1;
+    }
+    __syncthreads();
     // all of the thread's slots at once, so that their lookup and load chains overlap
 #pragma unroll
     for (int k = 0; k < (1000 + TB - 1) / TB; ++k) {
       const int sl = threadIdx.x + k * TB;
       if (sl < 1000) {
-        const int tx = sl % 10, ty = (sl / 10) % 10, tz = sl / 100;
-        const int u = band_lookup(B, 8 * bi + tx - 1, 8 * bj + ty - 1, 8 * bk + tz - 1);
+        const int gx = sl % 10 - 1, gy = (sl / 10) % 10 - 1, gz = sl / 100 - 1;  // in [-1, 8] per axis
+        const int dx = (gx > 7) - (gx < 0), dy = (gy > 7) - (gy < 0), dz = (gz > 7) - (gz < 0);
+        const int r = nrank[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)];
+        const int l = (gx - 8 * dx) + 8 * (gy - 8 * dy) + 64 * (gz - 8 * dz);
+        int u = -1;
+        if (r >= 0) {
+          const MetaWord m = B.meta[16 * r + (l >> 5)];
+          const uint32_t bit = 1u << (l & 31);
+          if (m.bits & bit) u = m.base + __popc(m.bits & (bit - 1u));
+        }
 #pragma unroll
         for (int c = 0; c < C; ++c) tile[sl * C + c] = u >= 0 ? X[(size_t)u * C + c] : TI(0);
       }

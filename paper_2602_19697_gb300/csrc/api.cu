@@ -147,6 +147,7 @@ void bf_destroy(bf_ctx* ctx) {
   if (ctx->mesh_t) cudaFree(ctx->mesh_t);
   if (ctx->mc_table) cudaFree(ctx->mc_table);
   if (ctx->mc_ntri) cudaFree(ctx->mc_ntri);
+  if (ctx->d_err) cudaFree(ctx->d_err);
   for (BlockGraph* g : ctx->blk) block_graph_free(g);
   for (SolveGraph* g : ctx->sgl) solve_graph_free(g);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);

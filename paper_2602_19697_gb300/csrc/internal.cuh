@@ -64,6 +64,7 @@ struct bf_ctx {
   std::string err;
   Workspace ws[WS_COUNT];
   int32_t* h_pinned = nullptr;  // small pinned scratch for scalars read back
+  int* d_err = nullptr;         // device word set by a kernel whose bounded wait ran out
   // last extracted mesh
   float* mesh_v = nullptr;
   int32_t* mesh_t = nullptr;

@@ -165,7 +165,8 @@ __device__ __forceinline__ T nsum(const T* t, int c) {
   return ((t[c - 1] + t[c + 1]) + (t[c - 10] + t[c + 10])) + (t[c - 100] + t[c + 100]);
 }
 
-// y = Q x (plain SpMV, FP32).  A CTA walks bricks b, b + grid, ...; the x
+// y = Q x (plain SpMV, FP32) for x not on a 16-byte boundary (k_spmv_t below
+// takes aligned arrays).  A CTA walks bricks b, b + grid, ...; the x
 // and Q_jj loads of the next brick are issued while the current brick is
 // formed, its lookup words (own and six neighbours) one brick earlier and the
 // neighbour ranks one brick earlier still, so no round trip to memory is
@@ -321,6 +322,220 @@ __global__ void __launch_bounds__(BT, SPMV_OCC) k_spmv(BandView B, float lam, co
     }
     __syncthreads();  // tile and this iteration's lookup buffer are free again
     cur = nxt;
+  }
+}
+
+// y = Q x (plain SpMV, FP32), one warp per brick, the brick's runs staged by
+// bulk copies.  Lane (lx, q) = lx + 8 q holds the brick's 16 voxels (lx, q +
+// 4 h, lz), slot s = 2 lz + h, i.e. local index lane + 32 s: slot s is exactly
+// lookup word s, so the lane's rank in the brick's compact run is (word base
+// - run start) + popc(bits below the lane), and the present lanes of a slot
+// read consecutive words of the staged run (no bank conflicts) and store a
+// contiguous run of y.  The z neighbours are the lane's own slots s -+ 2; the
+// x and y neighbours come by shuffles in the warp, the lane at the end of a
+// row or column handing out the neighbour brick's face value in place of its
+// own; the faces are gathered packed (64 values of a face pair per load) from
+// global memory and handed to the end lanes by one more shuffle.
+//
+// Each warp walks bricks b, b + W, ... (W warps in the grid): while brick b_i
+// is formed, lane 0 arms the other buffer's mbarrier and lanes 0-8 issue the
+// bulk copies of b_{i+1}: its x and Q_jj runs (from the 16-byte granule at or
+// below the run start up to the granule end at or above the run end, clipped
+// to the last whole granule of the arrays; the clipped tail is read directly)
+// and the 128-byte lookup blocks of the brick and of its six face neighbours
+// (zeros for a missing one); the neighbour ranks and run bounds of b_{i+2} are
+// loaded into registers.  A wait that runs out sets *err and ends the warp
+// after its copies in flight have landed (or a second wait has run out).
+constexpr int SPT = 4;        // warps per CTA
+constexpr int SPT_OCC = 4;    // resident CTAs per SM (124 registers)
+constexpr int SPT_RUN = 528;  // staged run capacity (floats): 512 + two granule slacks, 16-byte multiple
+
+struct __align__(16) SptBuf {
+  float xr[2][SPT_RUN];
+  float qr[2][SPT_RUN];
+  MetaWord m[2][7][16];  // the brick (0) and its face neighbours -x, +x, -y, +y, -z, +z (1-6)
+  uint64_t bar[2];
+};
+
+// lanes 0-5: face neighbour ranks of brick b; lanes 6, 7: its run bounds off[b], off[b + 1]
+__device__ __forceinline__ int spw_ranks(const BandView& B, int b, int lane) {
+  if (b >= B.NB || lane >= 8) return -1;
+  return lane < 6 ? __ldg(B.nbr + 6 * b + lane) : __ldg(B.off + b + lane - 6);
+}
+
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          (uint32_t)__cvta_generic_to_shared(sdst)),
+      "l"(gsrc), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// stage brick b (ranks and run bounds in lanes 0-7 of rk) into buffer k
+__device__ __forceinline__ void spt_stage(const BandView& B, int b, int rk, SptBuf& S, int k,
+                                          const float* __restrict__ x, const float* __restrict__ qd, int nfl,
+                                          int lane) {
+  const int o0 = __shfl_sync(0xffffffffu, rk, 6), o1 = __shfl_sync(0xffffffffu, rk, 7);
+  const int a0 = o0 & ~3, a1 = min((o1 + 3) & ~3, nfl);
+  const uint32_t bytes = a1 > a0 ? 4u * (uint32_t)(a1 - a0) : 0u;
+  // lanes 2-8: lookup block j = lane - 2 (the brick, then its neighbours from lanes 0-5 of rk)
+  const int j = lane - 2;
+  const int rj = __shfl_sync(0xffffffffu, rk, (j - 1) & 31);
+  const int r = j == 0 ? b : rj;
+  const bool meta_copy = lane >= 2 && lane < 9 && r >= 0;
+  const uint32_t nmeta = __popc(__ballot_sync(0xffffffffu, meta_copy));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of the buffer before the copies
+  if (lane == 0)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&S.bar[k])),
+                 "r"(2u * bytes + 128u * nmeta)
+                 : "memory");
+  if (lane < 2 && bytes) bulk_g2s(lane ? S.qr[k] : S.xr[k], (lane ? qd : x) + a0, bytes, &S.bar[k]);
+  if (meta_copy) bulk_g2s(S.m[k][j], B.meta + 16 * (size_t)r, 128u, &S.bar[k]);
+  if (lane >= 2 && lane < 9 && r < 0) {
+    int4* d = reinterpret_cast<int4*>(S.m[k][j]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) d[c] = make_int4(0, 0, 0, 0);
+  }
+}
+
+// value of x at local index 32 w + bit of the staged brick m16 (0 outside the band)
+__device__ __forceinline__ float face_x(const MetaWord* m16, const float* __restrict__ x, int w, int bit) {
+  const MetaWord m = m16[w];
+  return (m.bits >> bit) & 1u ? __ldg(x + m.base + __popc(m.bits & ((1u << bit) - 1u))) : 0.0f;
+}
+
+// One brick of k_spmv_t from its staged runs xr, qr (xr[0] = the run's first
+// voxel) and lookup words M[7][16]; o0 = the run start.  FULLB: all 512
+// voxels in the band, so slot s of the lane is run element lane + 32 s (no
+// rank arithmetic, no presence tests); otherwise the lane's rank in the run is
+// found from the slot's word, and a slot whose word is empty is skipped.
+template <bool FULLB>
+__device__ __forceinline__ void spt_brick(const MetaWord (*M)[16], const float* xr, const float* qr, int o0,
+                                          const float* __restrict__ x, float* __restrict__ y, float lam) {
+  constexpr unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, lx = lane & 7, q = lane >> 3;
+  const uint32_t below = (1u << lane) - 1u;
+  const int pside = lane >> 4, pc = lane & 7, pz = (lane >> 3) & 1;
+  const int sxm = (lane & 24) | ((lane - 1) & 7), sxp = (lane & 24) | ((lane + 1) & 7);
+  const int sym = (lane - 8) & 31, syp = (lane + 8) & 31;
+  const int sxf = (lx == 0 ? 16 : 0) + q, syf = (q == 0 ? 16 : 0) + lx;
+  int ix[16];  // rank of the lane's voxel in the run, or -1
+  float v[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    if (FULLB) {
+      ix[s] = lane + 32 * s;
+      v[s] = xr[ix[s]];
+    } else {
+      const MetaWord m = M[0][s];
+      ix[s] = (m.bits >> lane) & 1u ? m.base - o0 + __popc(m.bits & below) : -1;
+      v[s] = ix[s] >= 0 ? xr[ix[s]] : 0.0f;
+    }
+  }
+  // -z neighbour's plane lz = 7 (words 14, 15) and +z neighbour's plane 0 (words 0, 1), the lane's own (lx, ly)
+  float zf[4];
+  zf[0] = face_x(M[5], x, 14, lane);
+  zf[1] = face_x(M[5], x, 15, lane);
+  zf[2] = face_x(M[6], x, 0, lane);
+  zf[3] = face_x(M[6], x, 1, lane);
+  float XF[4], YF[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int lz = 2 * k + pz;
+    // x faces: local (7 or 0) + 8 ly + 64 lz with ly = pc: word 2 lz + (ly >> 2), bit (7 or 0) + 8 (ly & 3)
+    XF[k] = face_x(M[1 + pside], x, 2 * lz + (pc >> 2), (pside ? 0 : 7) + 8 * (pc & 3));
+    // y faces: local lx + 8 (7 or 0) + 64 lz with lx = pc: word 2 lz + (1 or 0), bit lx + (24 or 0)
+    YF[k] = face_x(M[3 + pside], x, 2 * lz + (pside ? 0 : 1), pc + (pside ? 0 : 24));
+  }
+#pragma unroll
+  for (int lz = 0; lz < 8; ++lz) {
+    // lanes q = 3 receive the -y face value (lx, lz), lanes q = 0 the +y one
+    const float yfv = __shfl_sync(FULL, YF[lz >> 1], syf + 8 * (lz & 1));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = 2 * lz + h;
+      if (!FULLB && M[0][s].bits == 0u) continue;  // no band voxel in this slot (warp-uniform)
+      const float c = v[s];
+      // lanes lx = 7 receive the -x face value (ly = q + 4h, lz), lanes lx = 0 the +x one
+      const float xfv = __shfl_sync(FULL, XF[lz >> 1], sxf + 8 * (lz & 1) + 4 * h);
+      const float xm = __shfl_sync(FULL, lx == 7 ? xfv : c, sxm);
+      const float xp = __shfl_sync(FULL, lx == 0 ? xfv : c, sxp);
+      // ly - 1 of lane q = 0 is lane q = 3 of the other half (h = 1) or the -y face (h = 0)
+      const float ym = __shfl_sync(FULL, q == 3 ? (h == 0 ? yfv : v[s - h]) : c, sym);
+      // ly + 1 of lane q = 3 is lane q = 0 of the other half (h = 0) or the +y face (h = 1)
+      const float yp = __shfl_sync(FULL, q == 0 ? (h == 0 ? v[s + 1 - h] : yfv) : c, syp);
+      const float zm = lz > 0 ? v[s - 2 * (lz > 0)] : zf[h];
+      const float zp = lz < 7 ? v[s + 2 * (lz < 7)] : zf[2 + h];
+      const float ns = ((xm + xp) + (ym + yp)) + (zm + zp);
+      if (FULLB || ix[s] >= 0) y[o0 + ix[s]] = qr[ix[s]] * c - lam * ns;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32 * SPT, SPT_OCC) k_spmv_t(BandView B, float lam, const float* __restrict__ qd,
+                                                               const float* __restrict__ x, float* __restrict__ y,
+                                                               int nfl, int* __restrict__ err) {
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ SptBuf sbuf[SPT];
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int nw = gridDim.x * SPT;
+  SptBuf& S = sbuf[wi];
+  int b = blockIdx.x * SPT + wi;
+  if (b >= B.NB) return;
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&S.bar[k]))
+                   : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  int rk = spw_ranks(B, b, lane);
+  spt_stage(B, b, rk, S, 0, x, qd, nfl, lane);
+  int o0 = __shfl_sync(FULL, rk, 6), o1 = __shfl_sync(FULL, rk, 7);  // run of the brick being formed
+  rk = spw_ranks(B, b + nw, lane);
+  for (int it = 0; b < B.NB; b += nw, ++it) {
+    const int cur = it & 1, bn = b + nw;
+    const int n0 = __shfl_sync(FULL, rk, 6), n1 = __shfl_sync(FULL, rk, 7);
+    if (bn < B.NB) spt_stage(B, bn, rk, S, cur ^ 1, x, qd, nfl, lane);
+    rk = spw_ranks(B, bn + nw, lane);
+    if (!bar_wait(&S.bar[cur], (uint32_t)(it >> 1) & 1u)) {
+      if (lane == 0) atomicOr(err, 1);
+      bar_wait(&S.bar[cur], (uint32_t)(it >> 1) & 1u);
+      if (bn < B.NB) bar_wait(&S.bar[cur ^ 1], (uint32_t)((it + 1) >> 1) & 1u);
+      return;
+    }
+    const int a0 = o0 & ~3, a1 = min((o1 + 3) & ~3, nfl);
+    if (o1 > a1) {  // the run reaches past the last whole granule: its tail read directly
+      const int t = max(a1, o0) + lane;
+      if (t < o1) {
+        S.xr[cur][t - a0] = __ldg(x + t);
+        S.qr[cur][t - a0] = __ldg(qd + t);
+      }
+      __syncwarp();
+    }
+    if (o1 - o0 == 512)
+      spt_brick<true>(S.m[cur], S.xr[cur] + (o0 - a0), S.qr[cur] + (o0 - a0), o0, x, y, lam);
+    else
+      spt_brick<false>(S.m[cur], S.xr[cur] + (o0 - a0), S.qr[cur] + (o0 - a0), o0, x, y, lam);
+    o0 = n0;
+    o1 = n1;
+    __syncwarp();  // the buffer of b_i is free for b_{i+2}
   }
 }
 
@@ -794,8 +1009,19 @@ bf_status solve_rhs_impl(bf_ctx* ctx, bf_band* b, const float* rhs, double tol, 
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   if (b->N == 0) return BF_OK;
   if (b->obs_mode == 3) return tri_spmv(ctx, b, x, y);
-  const int grid = b->NB < 152 * SPMV_OCC ? b->NB : 152 * SPMV_OCC;
-  k_spmv<<<grid, BT, 0, ctx->stream>>>(band_view(b), (float)b->prm.lambda, b->qd, x, y);
+  if ((((uintptr_t)x | (uintptr_t)b->qd) & 15u) == 0) {  // bulk copies need 16-byte aligned arrays
+    if (!ctx->d_err) {
+      BF_CK(cudaMalloc(&ctx->d_err, sizeof(int)));
+      BF_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    }
+    const int nw = (b->NB + SPT - 1) / SPT;
+    const int grid = nw < 152 * SPT_OCC ? nw : 152 * SPT_OCC;
+    k_spmv_t<<<grid, 32 * SPT, 0, ctx->stream>>>(band_view(b), (float)b->prm.lambda, b->qd, x, y,
+                                                   (int)(b->N & ~(int64_t)3), ctx->d_err);
+  } else {
+    const int grid = b->NB < 152 * SPMV_OCC ? b->NB : 152 * SPMV_OCC;
+    k_spmv<<<grid, BT, 0, ctx->stream>>>(band_view(b), (float)b->prm.lambda, b->qd, x, y);
+  }
   count_launch();
   BF_CK(cudaGetLastError());
   return BF_OK;

@@ -280,6 +280,14 @@ __global__ void __launch_bounds__(CT, res_occ<R>()) k_blk_res(const BlkArgs* __r
     const int nown = (t1 - t0) * F4, next = ne * F4;
 #pragma unroll
     for (int pp = 0; pp < NP; ++pp) {
+      // the probe values of this thread's rows in the stencil phase, loaded with the master iterates
+      __nv_bfloat162 zst[16 / RPS];
+#pragma unroll
+      for (int jstep = 0; jstep < 16 / RPS; ++jstep) {
+        const int row = t0 + 16 * wrp + jstep * RPS + lane / F4;
+        zst[jstep] = row < t1 ? *reinterpret_cast<const __nv_bfloat162*>(A->Z + (size_t)row * R + pp * CC + 2 * k2)
+                              : __floats2bfloat162_rn(0.f, 0.f);
+      }
       __syncthreads();  // the previous readers of sx4 are done
 #pragma unroll
       for (int i = 0; i < OWN; ++i) {
@@ -297,7 +305,7 @@ __global__ void __launch_bounds__(CT, res_occ<R>()) k_blk_res(const BlkArgs* __r
         if (q < next) sx4[SP_TR * F4 + q] = upd(ji[i], pp);
       }
       __syncthreads();
-#pragma unroll 1
+#pragma unroll
       for (int jstep = 0; jstep < 16 / RPS; ++jstep) {
         const int src = jstep * RPS + lane / F4;  // row of the warp's 16, and the lane holding its slots
         const int rr = 16 * wrp + src, row = t0 + rr;
@@ -320,7 +328,7 @@ __global__ void __launch_bounds__(CT, res_occ<R>()) k_blk_res(const BlkArgs* __r
             n1 = ff_add(n1, make_float2(v.z, v.w));
           }
           const int c0 = pp * CC + 2 * k2;
-          const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162*>(A->Z + (size_t)row * R + c0);
+          const __nv_bfloat162 zz = zst[jstep];
           const float z0 = __low2float(zz), z1 = __high2float(zz);
           const float2 xo0 = make_float2(xo.x, xo.y), xo1 = make_float2(xo.z, xo.w);
           const float2 qx0 = ff_add(ff_mul_f(xo0, q), ff_neg(ff_mul_f(n0, lam)));
@@ -543,7 +551,7 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __re
       const int q = threadIdx.x + i * CT;
       if (q >= nown) break;
       const size_t gq = (size_t)t0 * Q4 + q;
-      if (!INIT && q + CT < nown) {  // the thread's next item into L2
+      if (!INIT && OWN > blk_p1_unroll<R>() && q + CT < nown) {  // the thread's next item into L2 (one at a time)
         pf_l2(rA + gq + CT); pf_l2(wA + gq + CT); pf_l2(sA + gq + CT); pf_l2(p4 + gq + CT);
         if (!xhold && xread) pf_l2(x4 + gq + CT);
       }
@@ -593,12 +601,13 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __re
       us4[SP_TR * Q4 + q] = un;
     }
     __syncthreads();
-    if (!INIT) {  // the thread's first item of the next tile into L2
+    if (!INIT) {  // the next tile's own rows of r, w, s, p (and x) into L2, one bulk prefetch per vector
       const int tn = tile + gridDim.x;
-      if (tn < ntiles && (size_t)tn * SP_TR * Q4 + threadIdx.x < (size_t)N * Q4) {
-        const size_t gn = (size_t)tn * SP_TR * Q4 + threadIdx.x;
-        pf_l2(rA + gn); pf_l2(wA + gn); pf_l2(sA + gn); pf_l2(p4 + gn);
-        if (!xhold && xread) pf_l2(x4 + gn);
+      if (tn < ntiles && threadIdx.x < 5 && (threadIdx.x < 4 || (!xhold && xread))) {
+        const size_t n0 = (size_t)tn * SP_TR * Q4, n1 = min((size_t)N * Q4, n0 + (size_t)SP_TR * Q4);
+        const float4* v = threadIdx.x == 0 ? rA : threadIdx.x == 1 ? wA : threadIdx.x == 2 ? sA : threadIdx.x == 3 ? p4 : x4;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(v + n0), "r"((uint32_t)((n1 - n0) * 16))
+                     : "memory");
       }
     }
     // phase 3: w' = Q u' for the own rows, four columns (one float4 of u') per lane

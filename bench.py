@@ -45,7 +45,7 @@ METRIC = "posterior solve s (mean+diag var) at 1e-6 rel residual; SpMV GB/s vs H
 # DRAM bytes (read + write) per launch of the probe solver's iteration, from one ncu capture of that kernel on
 # the band it was taken on (dram__bytes_read.sum + dram__bytes_write.sum, mean of an x-writing and an x-holding
 # launch); keyed by (band voxels, block width); valid for the kernel as it was when captured.
-BLK_IT_TRAFFIC = {(7221796, 32): 9165044480}  # the object band at R = 32: 10.09 GB (x written) and 8.24 GB (held)
+BLK_IT_TRAFFIC = {(7221796, 32): 9167911552}  # the object band at R = 32: 10.10 GB (x written) and 8.24 GB (held)
 
 
 def parse():
@@ -358,6 +358,7 @@ def run_ours(args, world, rank, local):
     R_used, tune_ms = (R, None) if R else band.autotune_rhs_block(max(k1 - k0, 1))
     s = torch.empty(N, device=dev)
     band.estimate_variance(s, K=R_used, seed=0, rel_tol=args.tol, rhs_block=R_used)
+    band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R_used, reps=5)
     ms_iter = band.bench_kernel(bfsdf.BF_KERNEL_BLOCK_ITER, R=R_used, reps=20)
     # algorithmic bytes of one probe-solver iteration (per voxel row of R
     # columns): r, w, s, p read and p, r', s', w' written (32 B per column),
@@ -373,7 +374,7 @@ def run_ours(args, world, rank, local):
             "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
             "peak_kind": peak_kind, "traffic": traffic, "bytes_per_launch": bytes_it,
             "ms_per_launch": round(ms_iter, 5),
-            "timing": "20 back-to-back launches between CUDA events on the library stream (working set "
+            "timing": "20 back-to-back launches (after 5 untimed) between CUDA events on the library stream (working set "
                       f"{bytes_it / 1e9:.2f} GB per launch, larger than L2)"}
     spmv = spmv_roofline(band, stream, hbm, peak_kind)
     band.free()
@@ -475,7 +476,7 @@ def spmv_roofline(band, stream, hbm, peak_kind):
     nbytes = band.N * 12 + band.NB * 152
     gbs = nbytes / (float(np.median(ms)) * 1e-3) / 1e9
     del flush, clean
-    return {"kernel": "k_spmv (7-point SpMV, single RHS)", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+    return {"kernel": "k_spmv_t (7-point SpMV, single RHS: a warp per brick, runs bulk-copied)", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(gbs / hbm, 4), "peak_kind": peak_kind, "ms_median": round(float(np.median(ms)), 5),
             "bytes": nbytes, "bytes_per_voxel": round(nbytes / band.N, 3),
             "l2": "1 GB written, then another 1 GB read, before each of 20 single launches; median"}

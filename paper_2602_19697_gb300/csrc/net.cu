@@ -242,24 +242,30 @@ __global__ void __launch_bounds__(NT, 1) k_conv(int nb, const __nv_bfloat16* __r
 //
 // One CTA per SM walks the bricks.  The input tile lives in shared memory in
 // the canonical K-major, no-swizzle operand layout: plane c (channels
-// 8c .. 8c+7) holds one 16-byte row per padded voxel row p (12^3 tile with a
-// zero border, rows up to TC_ROWS), so the A operand of tap t for output rows
-// p0 .. p0+127 is the 128 rows starting at p0 + off(t): an 8-row core matrix
-// is 128 contiguous bytes (stride between core matrices along M: 128 B; along
-// K: one plane).  The weights are staged once, per tap and 8-channel chunk a
-// [C_out][8] block (the B operand, K-major).  Output rows cover the interior
-// rows [157, 157 + 12 x 128); each 128-row M tile accumulates in its own TMEM
-// columns (D: 128 lanes x C_out FP32), over 27 taps x C_in/16 MMAs of
-// M128 x N(C_out) x K16, issued by two threads (six tiles each), completed
-// through an mbarrier; the next brick's input is read into registers while
-// the MMAs run.
-// The epilogue (bias, ReLU / loss / ReLU mask) reads TMEM with tcgen05.ld and
-// writes the interior rows.
-constexpr int TC_P0 = 157;                 // first interior padded row
-constexpr int TC_MT = 12;                  // 128-row M tiles per brick
-constexpr int TC_ROWS = 1856;              // padded rows held (>= 157 + 1536 + 157)
+// 8c .. 8c+7) holds one 16-byte row per padded voxel row (12^3 tile with a
+// zero border, padded row TC_PB + (x+1) + 12 (y+1) + 144 (z+1)), so the A
+// operand of tap t for output rows p0 .. p0+127 is the 128 rows starting at
+// p0 + off(t): an 8-row core matrix is 128 contiguous bytes (stride between
+// core matrices along M: 128 B; along K: one plane).  The weights are staged
+// once, per tap and 8-channel chunk a [C_out][8] block (the B operand,
+// K-major).  One 128-row M tile per interior plane z: rows (x, y) = (-1..10,
+// 0..9) of the plane (120 rows holding its 100 voxels) and 8 rows of its
+// y = 10 border, 1.28 computed rows per voxel (the last layer, whose outputs
+// are needed at the 8^3 centre only, takes planes 1..8).  Each tile
+// accumulates in its own TMEM columns (D: 128 lanes x C_out FP32), over 27
+// taps x C_in/16 MMAs of M128 x N(C_out) x K16 issued by two threads
+// (alternate tiles; one thread issues too slowly): the first half of the
+// planes completes on one mbarrier, the second on another,
+// so the epilogue of the first half (bias, ReLU / loss / ReLU mask; TMEM read
+// by tcgen05.ld, interior voxels written) runs while the second half's MMAs
+// do; the next brick's input is read into registers meanwhile.
+// (With 32 input channels every MMA reads its 4 KB A block from shared
+// memory for 131 kFLOP, so the MMAs run at the shared-memory operand rate,
+// about half the tensor peak, rather than at the tensor peak.)
+constexpr int TC_PB = 16;                  // padded row offset (keeps the lowest tap row of plane 0 >= 0)
+constexpr int TC_ROWS = 1856;              // padded rows held
 constexpr int TC_NT = 256;                 // threads per CTA (two warpgroups)
-static_assert(TC_P0 + 128 * TC_MT + 157 <= TC_ROWS, "tile rows");
+static_assert(TC_PB + 156 - 157 >= 0 && TC_PB + 156 + 144 * 9 + 127 + 157 < TC_ROWS, "tile rows");
 
 template <int CIN, int COUT>
 __host__ __device__ constexpr size_t tc_smem() {
@@ -330,12 +336,14 @@ __global__ void __launch_bounds__(TC_NT, 1) k_conv_tc(int nb, const __nv_bfloat1
   extern __shared__ __align__(16) uint8_t tsm[];
   constexpr int NPL = CIN / 8;  // 8-channel planes of the input tile
   constexpr int KS = CIN / 16;  // K16 steps per tap
-  constexpr uint32_t TCOLS = COUT * TC_MT > 256 ? 512 : 256;
+  constexpr int Z0 = MODE == MODE_LAST ? 1 : 0, NTZ = MODE == MODE_LAST ? 8 : 10;  // planes computed
+  constexpr int NH = NTZ / 2;                                                         // planes per half
+  constexpr uint32_t TCOLS = NTZ * COUT > 256 ? 512 : (NTZ * COUT > 128 ? 256 : 128);
   __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(tsm);  // [NPL][TC_ROWS][8]
   __nv_bfloat16* wsm = act + (size_t)TC_ROWS * CIN;              // [27][NPL][COUT][8]
   float* bs = reinterpret_cast<float*>(wsm + (size_t)27 * CIN * COUT);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(bs + COUT);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // zero tile (the border rows stay zero), weights in operand order, bias
   for (int q = tid; q < TC_ROWS * CIN / 8; q += TC_NT) reinterpret_cast<uint4*>(act)[q] = make_uint4(0, 0, 0, 0);
@@ -344,9 +352,11 @@ __global__ void __launch_bounds__(TC_NT, 1) k_conv_tc(int nb, const __nv_bfloat1
     reinterpret_cast<uint4*>(wsm)[(tap * NPL + c) * COUT + co] = reinterpret_cast<const uint4*>(w)[q];
   }
   for (int q = tid; q < COUT; q += TC_NT) bs[q] = (bias && q < nbias) ? bias[q] : 0.0f;
-  if (tid == 0) {
-    // two arrivals per phase: the commits of the two issuing threads
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"((uint32_t)__cvta_generic_to_shared(mbar)) : "memory");
+  if (tid == 0) {  // two arrivals per phase (the commits of the two issuing threads), for each half of the planes
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"((uint32_t)__cvta_generic_to_shared(mbar + h))
+                   : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -375,25 +385,27 @@ __global__ void __launch_bounds__(TC_NT, 1) k_conv_tc(int nb, const __nv_bfloat1
   };
   load_brick(blockIdx.x);
   const uint64_t ad0 = tc_desc(act_s, TC_ROWS * 16u, 128u), bd0 = tc_desc(w_s, COUT * 16u, 128u);
-  int it = 0;
-  for (int b = blockIdx.x; b < nb; b += gridDim.x, ++it) {
-    // the brick's 1000 rows into the interior of the tile (the previous MMAs have read the tile)
+  // the brick's 1000 rows into the interior of the tile (the MMAs of the previous brick have read the tile)
+  auto stage = [&]() {
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
       const int q = tid + i * TC_NT;
       if (q < TV * NPL) {
         const int v = q / NPL, c = q - v * NPL;
-        reinterpret_cast<uint4*>(act)[(size_t)c * TC_ROWS + prow(v)] = pre[i];
+        reinterpret_cast<uint4*>(act)[(size_t)c * TC_ROWS + TC_PB + prow(v)] = pre[i];
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if ((tid & 127) == 0) {  // two issuing threads, six M tiles each; descriptors advance by 16-byte units
+  };
+  // the MMAs of half h of the planes: two issuing threads, alternate tiles; descriptors in 16-byte units
+  auto issue = [&](int h) {
+    if ((tid & 127) == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int m0 = (tid >> 7) * (TC_MT / 2);
-      for (int mt = m0; mt < m0 + TC_MT / 2; ++mt) {
-        const int p0 = TC_P0 + 128 * mt;
+#pragma unroll 1
+      for (int mt = h * NH + ((h * NH + (tid >> 7)) & 1); mt < (h + 1) * NH; mt += 2) {
+        const int p0 = TC_PB + 156 + 144 * (Z0 + mt);  // row of (x, y, z) = (-1, 0, Z0 + mt)
         for (int tap = 0; tap < 27; ++tap) {
           const uint64_t ar = ad0 + (uint64_t)(p0 + tap_off(tap));
 #pragma unroll
@@ -402,19 +414,27 @@ __global__ void __launch_bounds__(TC_NT, 1) k_conv_tc(int nb, const __nv_bfloat1
                    bd0 + (uint64_t)((tap * NPL + 2 * ks) * COUT), tc_idesc<COUT>(), (tap | ks) != 0);
         }
       }
-      tc_commit(mbar);
+      tc_commit(mbar + h);
     }
-    load_brick(b + gridDim.x);
-    const bool ok = tc_wait(mbar, (uint32_t)it & 1u);
-    if (__syncthreads_or(!ok)) {  // the MMAs did not complete in time: report and stop
+  };
+  // wait for half h of brick number `it`; a wait that runs out reports, waits once more for every MMA in
+  // flight (halves h..1 of this brick) and returns false in all threads
+  auto wait_half = [&](int h, int it) -> bool {
+    const bool ok = tc_wait(mbar + h, (uint32_t)it & 1u);
+    if (__syncthreads_or(!ok)) {
       if (tid == 0) atomicExch(err, 1);
-      break;
+      for (int hh = h; hh < 2; ++hh) tc_wait(mbar + hh, (uint32_t)it & 1u);
+      return false;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warpgroup g takes M tiles g, g + 2, ...; warp w reads TMEM lanes 32 (w % 4) ..
+    return true;
+  };
+  // epilogue of half h of brick b: warpgroup g takes the half's tiles g, g + 2, ...; warp w reads TMEM lanes
+  // 32 (w % 4) ..
+  auto epilogue = [&](int h, int b) {
     const int lq = warp & 3;
-    for (int mt = warp >> 2; mt < TC_MT; mt += 2) {
-      const int p = TC_P0 + 128 * mt + 32 * lq + lane;
+    for (int mt = h * NH + (warp >> 2); mt < (h + 1) * NH; mt += 2) {
+      const int z = Z0 + mt, i = 32 * lq + lane;  // tile row i: (x, y) = (i % 12 - 1, i / 12)
       const uint32_t taddr = tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(mt * COUT);
       float acc[COUT];
 #pragma unroll
@@ -424,9 +444,8 @@ __global__ void __launch_bounds__(TC_NT, 1) k_conv_tc(int nb, const __nv_bfloat1
 #pragma unroll
         for (int k = 0; k < 16; ++k) acc[k0 + k] = t[k];
       }
-      const int px = p % 12, py = (p / 12) % 12, pz = p / 144;
-      if (px < 1 || px > 10 || py < 1 || py > 10 || pz < 1 || pz > 10) continue;
-      const int v = (px - 1) + 10 * (py - 1) + 100 * (pz - 1);
+      if (i >= 120 || i % 12 == 0 || i % 12 == 11) continue;  // the x = -1, 10 columns and the y = 10 row
+      const int v = (i % 12 - 1) + 10 * (i / 12) + 100 * z;
       const size_t o = ((size_t)b * TV + v) * COUT;
 #pragma unroll
       for (int co = 0; co < COUT; ++co) acc[co] += bs[co];
@@ -480,8 +499,36 @@ __global__ void __launch_bounds__(TC_NT, 1) k_conv_tc(int nb, const __nv_bfloat1
         reinterpret_cast<uint4*>(y + o)[c8] = o4;
       }
     }
+  };
+  // pipeline over the CTA's bricks: the first half of the next brick's planes runs on the tensor cores while
+  // the epilogue of this brick's second half does
+  int b = blockIdx.x, it = 0;
+  if (b < nb) {
+    stage();
+    issue(0);
+    issue(1);
+    load_brick(b + gridDim.x);
+  }
+  for (; b < nb; b += gridDim.x, ++it) {
+    if (!wait_half(0, it)) break;
+    if (MODE == MODE_LAST) {  // dL/do is zero on planes 0 and 9, which the last layer does not compute
+      for (int q = tid; q < 200 * COUT / 8; q += TC_NT) {
+        const int vv = q / (COUT / 8), v = vv < 100 ? vv : vv + 800;
+        reinterpret_cast<uint4*>(y + ((size_t)b * TV + v) * COUT)[q % (COUT / 8)] = make_uint4(0, 0, 0, 0);
+      }
+    }
+    epilogue(0, b);
+    if (!wait_half(1, it)) break;
+    const int bn = b + gridDim.x;
+    if (bn < nb) {
+      stage();  // also: every thread is past the first half's epilogue, whose TMEM columns are reused
+      issue(0);
+      load_brick(bn + gridDim.x);
+    }
+    epilogue(1, b);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // TMEM reads and tile reads of this brick are done
+    __syncthreads();  // the second half's TMEM columns are read
+    if (bn < nb) issue(1);
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

@@ -601,9 +601,9 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __re
       us4[SP_TR * Q4 + q] = un;
     }
     __syncthreads();
-    if (!INIT) {  // the next tile's own rows of r, w, s, p (and x) into L2, one bulk prefetch per vector
+    {  // the next tile's own rows of r, w, s, p (and x; the start pass: r only) into L2, one bulk prefetch per vector
       const int tn = tile + gridDim.x;
-      if (tn < ntiles && threadIdx.x < 5 && (threadIdx.x < 4 || (!xhold && xread))) {
+      if (tn < ntiles && threadIdx.x < (INIT ? 1 : 5) && (threadIdx.x < 4 || (!xhold && xread))) {
         const size_t n0 = (size_t)tn * SP_TR * Q4, n1 = min((size_t)N * Q4, n0 + (size_t)SP_TR * Q4);
         const float4* v = threadIdx.x == 0 ? rA : threadIdx.x == 1 ? wA : threadIdx.x == 2 ? sA : threadIdx.x == 3 ? p4 : x4;
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(v + n0), "r"((uint32_t)((n1 - n0) * 16))
@@ -750,17 +750,29 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __re
 template <int R>
 __global__ void k_probes(int N, const int32_t* __restrict__ lin, uint64_t mseed, int k0, int ncols,
                          __nv_bfloat16* __restrict__ Z, float* __restrict__ r0) {
-  const int64_t n = (int64_t)N * R;
+  // a thread forms 8 consecutive columns of one row: one 16-byte store of Z, two of r
+  constexpr int G = R / 8;  // column groups per row
+  const int64_t n = (int64_t)N * G;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e / R;
-    int c = (int)(e - i * R);
-    float z = 0.0f;
-    if (c < ncols) {
-      uint64_t v = mix64(mseed ^ ((uint64_t)(k0 + c) * 0xD1B54A32D192ED03ULL) ^ (uint64_t)(uint32_t)lin[i]);
-      z = (v >> 63) ? -1.0f : 1.0f;
+    const int64_t i = e / G;
+    const int c0 = (int)(e - i * G) * 8;
+    const uint64_t li = (uint64_t)(uint32_t)__ldg(lin + i);
+    float z[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      z[k] = 0.0f;
+      if (c0 + k < ncols) {
+        const uint64_t v = mix64(mseed ^ ((uint64_t)(k0 + c0 + k) * 0xD1B54A32D192ED03ULL) ^ li);
+        z[k] = (v >> 63) ? -1.0f : 1.0f;
+      }
     }
-    Z[e] = __float2bfloat16(z);
-    r0[e] = z;
+    uint4 zb;
+    __nv_bfloat162* zh = reinterpret_cast<__nv_bfloat162*>(&zb);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) zh[k] = __floats2bfloat162_rn(z[2 * k], z[2 * k + 1]);
+    reinterpret_cast<uint4*>(Z)[e] = zb;
+    reinterpret_cast<float4*>(r0)[2 * e] = make_float4(z[0], z[1], z[2], z[3]);
+    reinterpret_cast<float4*>(r0)[2 * e + 1] = make_float4(z[4], z[5], z[6], z[7]);
   }
 }
 
@@ -1202,12 +1214,11 @@ static bf_status variance_t(bf_ctx* ctx, bf_band* b, int kb, int ke, double scal
   }
   int tot_it = 0;
   bf_status result = BF_OK;
-  const int64_t NR = (int64_t)N * R;
-  const unsigned gNR = grid_for(NR, 256, 152 * 32);
   for (int k0 = kb; k0 < ke; k0 += R) {
     // one block of R probes: float-float master iterates, FP32 correction solves
     int ncols = ke - k0 < R ? ke - k0 : R;
-    k_probes<R><<<gNR, 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z, g->h.r[0]);
+    k_probes<R><<<grid_for((int64_t)N * (R / 8), 256, 152 * 16), 256, 0, s>>>(N, b->lin, mseed, k0, ncols, g->Z,
+                                                                         g->h.r[0]);
     count_launch();
     k_blk_init<<<1, MAXR, 0, s>>>(g->st, tol, max_iter, ncols, N, ETA_MIN, sq != nullptr);
     count_launch();

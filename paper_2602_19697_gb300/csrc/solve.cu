@@ -242,7 +242,8 @@ __device__ __forceinline__ void spmv_issue(const MetaWord (*sm)[16], const float
 }
 
 // bring bytes of v[i0 .. i1) into L2 as whole lines (bulk prefetch of the 16-byte granules inside the range)
-__device__ __forceinline__ void prefetch_range(const float* v, int64_t i0, int64_t i1) {
+template <class E>
+__device__ __forceinline__ void prefetch_range(const E* v, int64_t i0, int64_t i1) {
   const uint64_t a0 = ((uint64_t)(v + i0) + 15u) & ~(uint64_t)15u, a1 = (uint64_t)(v + i1) & ~(uint64_t)15u;
   if (a1 > a0)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
@@ -701,12 +702,28 @@ __global__ void __launch_bounds__(BT, CG_OCC) k_cg(const SolveArgs<T>* __restric
   // lookup words of the next brick fetched during the current one (as in k_spmv)
   MetaWord nm = meta_word(B, meta_rank(B, blockIdx.x));
   int nr = meta_rank(B, blockIdx.x + gridDim.x);
+  // threads 0-5: the run bounds of the next brick, whose runs of r, w, s, p, x and Q_jj they prefetch into L2
+  // while this brick is formed (the bounds of the brick after it loaded meanwhile)
+  int2 pr = make_int2(0, 0);
+  if (threadIdx.x < 6 && (int)(blockIdx.x + gridDim.x) < B.NB)
+    pr = make_int2(__ldg(B.off + blockIdx.x + gridDim.x), __ldg(B.off + blockIdx.x + gridDim.x + 1));
   for (int b = blockIdx.x; b < B.NB; b += gridDim.x) {
     __syncthreads();
     if (threadIdx.x < 7 * 16) sm[threadIdx.x >> 4][threadIdx.x & 15] = nm;
     __syncthreads();
     nm = meta_word(B, nr);
     nr = meta_rank(B, b + 2 * gridDim.x);
+    if (threadIdx.x < 6) {
+      if (pr.y > pr.x) {
+        const int t = threadIdx.x;
+        if (t < 5)
+          prefetch_range(t == 0 ? r_in : t == 1 ? w_in : t == 2 ? s_in : t == 3 ? (const T*)p : (const T*)x, pr.x, pr.y);
+        else
+          prefetch_range(qd, pr.x, pr.y);
+      }
+      const int bn2 = b + 2 * gridDim.x;
+      pr = bn2 < B.NB ? make_int2(__ldg(B.off + bn2), __ldg(B.off + bn2 + 1)) : make_int2(0, 0);
+    }
     int idx[4];
     T rn[4], un[4];
 #pragma unroll

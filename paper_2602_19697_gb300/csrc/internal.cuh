@@ -285,6 +285,14 @@ __device__ __forceinline__ Ray pixel_ray(const Pose& P, int px, int py, const In
   return q;
 }
 
+// bring bytes of v[i0 .. i1) into L2 as whole lines (bulk prefetch of the 16-byte granules inside the range)
+template <class E>
+__device__ __forceinline__ void prefetch_range(const E* v, int64_t i0, int64_t i1) {
+  const uint64_t a0 = ((uint64_t)(v + i0) + 15u) & ~(uint64_t)15u, a1 = (uint64_t)(v + i1) & ~(uint64_t)15u;
+  if (a1 > a0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
+}
+
 // compact index of voxel (i,j,k) or -1 if outside the band
 __device__ __forceinline__ int band_lookup(const BandView& B, int i, int j, int k) {
   if ((unsigned)i >= (unsigned)B.n || (unsigned)j >= (unsigned)B.n || (unsigned)k >= (unsigned)B.n) return -1;

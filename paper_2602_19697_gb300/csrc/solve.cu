@@ -241,13 +241,6 @@ __device__ __forceinline__ void spmv_issue(const MetaWord (*sm)[16], const float
   }
 }
 
-// bring bytes of v[i0 .. i1) into L2 as whole lines (bulk prefetch of the 16-byte granules inside the range)
-template <class E>
-__device__ __forceinline__ void prefetch_range(const E* v, int64_t i0, int64_t i1) {
-  const uint64_t a0 = ((uint64_t)(v + i0) + 15u) & ~(uint64_t)15u, a1 = (uint64_t)(v + i1) & ~(uint64_t)15u;
-  if (a1 > a0)
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
-}
 
 // Software pipeline over the CTA's bricks b0, b1 = b0 + grid, ...: in the
 // iteration of brick b_i the tile receives b_i's values (loaded during the

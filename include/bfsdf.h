@@ -146,8 +146,8 @@ bf_status bf_integrate_depth(bf_ctx* ctx, bf_band* band, const float* depth, int
 #define BF_INTEGRATE_DETERMINISTIC 1u
 
 /* Trilinear observation rows (Sec. 3.5: each observation is a linear row over
- * the voxel values with up to 8 non-zeros, the trilinear interpolation
- * weights of the sample point; Sec. 3.6 precision equation: A^T W A then
+ * the voxel values holding the eight trilinear interpolation weights of the
+ * sample point, one per corner of its cell; Sec. 3.6 precision equation: A^T W A then
  * couples each voxel with its 26 neighbours, so Q is a 27-point stencil with
  * per-voxel coefficients).  Flag of bf_integrate_depth_ex: the band
  * accumulates these rows instead of the voxel-binned ones.

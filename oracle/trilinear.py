@@ -1,5 +1,5 @@
-"""Trilinear observation rows (Sec. 3.5: the linear relation y_i ~ a_i^T x with
-up to 8 non-zeros per row for trilinear interpolation) and the posterior
+"""Trilinear observation rows (Sec. 3.5: the linear relation y_i ~ a_i^T x whose
+row holds the eight trilinear weights of the sample point, one per cell corner) and the posterior
 system they give (Sec. 3.6: Q = Q0 + A^T W A, h = A^T W y + b0).
 
 TEST INFRASTRUCTURE: the FP64 reference of the trilinear form of the

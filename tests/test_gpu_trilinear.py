@@ -1,5 +1,5 @@
 """GPU parity of the trilinear observation rows and the 27-point precision
-(Sec. 3.5 linear row with up to 8 non-zeros; Sec. 3.6 precision and mean
+(Sec. 3.5 linear row of trilinear weights, one per cell corner; Sec. 3.6 precision and mean
 equations; Sec. 3.7 estimator) against oracle/trilinear.py.
 
 Bars: the rows (cells, weights, which samples count) bit-exact against the

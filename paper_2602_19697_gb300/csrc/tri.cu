@@ -2,7 +2,7 @@
 //
 // Sec. 3.5 writes each depth observation as a linear row a_i over the voxel
 // values holding the trilinear interpolation weights of the sample point,
-// one per voxel centre of the cell of the 8 voxel centres around it.  Then A^T W A
+// one for each of the 8 voxel centres of the cell around it.  Then A^T W A
 // (Sec. 3.6 precision equation) couples every voxel with its 26 neighbours
 // and Q = lambda L + lambda_b I_dB + A^T W A is a 27-point stencil with
 // per-voxel coefficients; h = A^T W y + b0 as before.

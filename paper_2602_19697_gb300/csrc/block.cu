@@ -454,6 +454,10 @@ __device__ __forceinline__ float4 scale4(float4 a, float q) {
 //   phase 2, the external rows its face neighbours reference: u' from their
 //     (old) r, w, s by the same arithmetic
 //   phase 3, w' = Q u' for the own rows from the staged u'; partial w'.u'.
+// Streaming traffic that no other tile of the launch reads again (the own
+// rows' p and x, and every row written) goes through evict-first loads and
+// stores, leaving L2 to the r, w, s lines that other tiles gather as external
+// rows.
 // INIT (start of a correction solve from r): u = r/Q_jj, w = Q u, written to
 // w[par]; r stays, x is zero, and p and s are not read by the next iteration
 // (beta = 0 there).  Otherwise r, w, s are double-buffered (read [par],
@@ -562,21 +566,21 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __re
         rn = ri;
         un = scale4(ri, qi);
       } else {
-        const float4 wi = wA[gq], si = sA[gq], pi = p4[gq];
+        const float4 wi = wA[gq], si = sA[gq], pi = __ldcs(p4 + gq);
         const float4 u0 = scale4(ri, qi);
         const float4 pn = make_float4(__fadd_rn(u0.x, bmul(be.x, pi.x)), __fadd_rn(u0.y, bmul(be.y, pi.y)),
                                       __fadd_rn(u0.z, bmul(be.z, pi.z)), __fadd_rn(u0.w, bmul(be.w, pi.w)));
         const float4 sn = next_s(wi, si, be);
         rn = next_r(ri, sn, al);
         un = scale4(rn, qi);
-        p4[gq] = pn;
+        __stcs(p4 + gq, pn);
         if (!xhold) {
-          const float4 xi = xread ? x4[gq] : make_float4(0.f, 0.f, 0.f, 0.f);
-          x4[gq] = make_float4(fmaf(al.x, pn.x, fmaf(ap.x, pi.x, xi.x)), fmaf(al.y, pn.y, fmaf(ap.y, pi.y, xi.y)),
-                               fmaf(al.z, pn.z, fmaf(ap.z, pi.z, xi.z)), fmaf(al.w, pn.w, fmaf(ap.w, pi.w, xi.w)));
+          const float4 xi = xread ? __ldcs(x4 + gq) : make_float4(0.f, 0.f, 0.f, 0.f);
+          __stcs(x4 + gq, make_float4(fmaf(al.x, pn.x, fmaf(ap.x, pi.x, xi.x)), fmaf(al.y, pn.y, fmaf(ap.y, pi.y, xi.y)),
+                               fmaf(al.z, pn.z, fmaf(ap.z, pi.z, xi.z)), fmaf(al.w, pn.w, fmaf(ap.w, pi.w, xi.w))));
         }
-        sB[gq] = sn;
-        rB[gq] = rn;
+        __stcs(sB + gq, sn);
+        __stcs(rB + gq, rn);
       }
       us4[q] = un;
       fa[0] += rn.x * un.x; fa[1] += rn.y * un.y; fa[2] += rn.z * un.z; fa[3] += rn.w * un.w;
@@ -642,7 +646,7 @@ __global__ void __launch_bounds__(CT, blk_occ<R>()) k_blk_it(const BlkArgs* __re
       wn.y = q * uo.y - lam * ns.y;
       wn.z = q * uo.z - lam * ns.z;
       wn.w = q * uo.w - lam * ns.w;
-      reinterpret_cast<float4*>(wB)[(size_t)row * Q4 + g] = wn;
+      __stcs(reinterpret_cast<float4*>(wB) + (size_t)row * Q4 + g, wn);
       ft[0] += wn.x * uo.x; ft[1] += wn.y * uo.y; ft[2] += wn.z * uo.z; ft[3] += wn.w * uo.w;
     }
   }

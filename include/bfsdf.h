@@ -206,7 +206,12 @@ bf_status bf_reset_observations(bf_ctx* ctx, bf_band* band);
 bf_status bf_export_system(bf_ctx* ctx, const bf_band* band, float* d, float* hdata, float* qdiag, float* rhs);
 
 /* y = Q x for x, y [N] float (Sec. 3.6 precision equation; matrix-free
- * 7-point stencil: (Qx)_j = Q_jj x_j - lambda sum_{6-nbrs k in B} x_k). */
+ * 7-point stencil: (Qx)_j = Q_jj x_j - lambda sum_{6-nbrs k in B} x_k).
+ * x, y device or host (host memory is staged; with a host y the call is
+ * synchronous).  For x on a 16-byte boundary the kernel stages each brick's
+ * runs by bulk copies whose waits are bounded: a wait that ran out (not
+ * expected) is reported as BF_ECUDA by the next synchronous bf_spmv (host y)
+ * or bf_bench_kernel call on the context. */
 bf_status bf_spmv(bf_ctx* ctx, const bf_band* band, const float* x, float* y);
 
 /* Y = Q X for R right-hand sides at once (Sec. 3.6 precision equation, the

@@ -328,7 +328,8 @@ bf_status bf_spmv(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   BF_TRY(stage_in(ctx, x, b->N, WS_STAGE2, &dx));
   BF_TRY(stage_out(ctx, y, b->N, WS_OUT0, &dy, &host));
   BF_TRY(spmv_launch(ctx, b, dx, dy));
-  return copy_out(ctx, y, (const float*)dy, b->N, host);
+  BF_TRY(copy_out(ctx, y, (const float*)dy, b->N, host));
+  return host ? device_wait_status(ctx, "bf_spmv") : BF_OK;  // host output: the call is synchronous anyway
 }
 
 bf_status bf_spmm(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y) {
@@ -564,7 +565,7 @@ bf_status bf_bench_kernel(bf_ctx* ctx, bf_band* b, int which, int R, int reps, d
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *ms_per_launch = t / reps;
-    return BF_OK;
+    return device_wait_status(ctx, "bf_bench_kernel");
   }
   if (which == BF_KERNEL_BLOCK_ITER) return bench_block_iter(ctx, b, R, reps, ms_per_launch);
   return bf_fail(ctx, BF_EINVAL, "bf_bench_kernel: unknown kernel");

@@ -213,6 +213,9 @@ bf_status tri_variance(bf_ctx* ctx, bf_band* b, int kb, int ke, double scale, ui
 constexpr int TRI_R = 8;  // probe columns per block of the trilinear probe solver
 bf_status band_observations_f64(bf_ctx* ctx, const bf_band* b, double* d64, double* h64);
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y);
+// After the stream has been synchronised: BF_ECUDA if a kernel's bounded wait ran out since the last check
+// (the context's device error word, which is then cleared), else BF_OK.
+bf_status device_wait_status(bf_ctx* ctx, const char* what);
 bf_status spmm_launch(bf_ctx* ctx, bf_band* b, const float* X, int R, float* Y);
 bf_status solve_mean_impl(bf_ctx* ctx, bf_band* b, double tol, int max_iter, unsigned flags, float* mu, int* iters,
                           double* relres);

@@ -1016,6 +1016,16 @@ bf_status solve_rhs_impl(bf_ctx* ctx, bf_band* b, const float* rhs, double tol, 
   return solve_t<float>(ctx, b, tol, max_iter, 0u, x, iters, relres, rhs);
 }
 
+bf_status device_wait_status(bf_ctx* ctx, const char* what) {
+  if (!ctx->d_err) return BF_OK;
+  BF_CK(cudaMemcpyAsync(ctx->h_pinned, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  BF_CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->h_pinned[0] == 0) return BF_OK;
+  ctx->h_pinned[0] = 0;
+  BF_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+  return bf_fail(ctx, BF_ECUDA, what, "a kernel's bounded wait for its bulk copies ran out (results not valid)");
+}
+
 bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   if (b->N == 0) return BF_OK;
   if (b->obs_mode == 3) return tri_spmv(ctx, b, x, y);

@@ -45,7 +45,7 @@ METRIC = "posterior solve s (mean+diag var) at 1e-6 rel residual; SpMV GB/s vs H
 # DRAM bytes (read + write) per launch of the probe solver's iteration, from one ncu capture of that kernel on
 # the band it was taken on (dram__bytes_read.sum + dram__bytes_write.sum, mean of an x-writing and an x-holding
 # launch); keyed by (band voxels, block width); valid for the kernel as it was when captured.
-BLK_IT_TRAFFIC = {(7221796, 32): 9167911552}  # the object band at R = 32: 10.10 GB (x written) and 8.24 GB (held)
+BLK_IT_TRAFFIC = {(7221796, 32): 9154034688}  # the object band at R = 32: 10.08 GB (x written) and 8.23 GB (held)
 
 
 def parse():

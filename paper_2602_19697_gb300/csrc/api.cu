@@ -133,6 +133,15 @@ bf_status bf_create(int device, void* stream, bf_ctx** out) {
     delete ctx;
     return BF_ENOMEM;
   }
+  // the device error word of the kernels with bounded waits (allocated here, so that no later call allocates it)
+  if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess ||
+      cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaFreeHost(ctx->h_pinned);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+    return BF_ENOMEM;
+  }
   *out = ctx;
   return BF_OK;
 }

@@ -1030,10 +1030,6 @@ bf_status spmv_launch(bf_ctx* ctx, const bf_band* b, const float* x, float* y) {
   if (b->N == 0) return BF_OK;
   if (b->obs_mode == 3) return tri_spmv(ctx, b, x, y);
   if ((((uintptr_t)x | (uintptr_t)b->qd) & 15u) == 0) {  // bulk copies need 16-byte aligned arrays
-    if (!ctx->d_err) {
-      BF_CK(cudaMalloc(&ctx->d_err, sizeof(int)));
-      BF_CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
-    }
     const int nw = (b->NB + SPT - 1) / SPT;
     const int grid = nw < 152 * SPT_OCC ? nw : 152 * SPT_OCC;
     k_spmv_t<<<grid, 32 * SPT, 0, ctx->stream>>>(band_view(b), (float)b->prm.lambda, b->qd, x, y,
